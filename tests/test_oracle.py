@@ -1,0 +1,377 @@
+"""Pins for the FP64 oracle (CPU only).
+
+Each test ties the oracle to something other than itself: the exact
+vertex enumeration of Section 3.2 against the independent dense simplex of
+Section 3.1 (and scipy's HiGHS LP), closed forms, invariances of the
+objective, the duality-gap certificate and finite differences.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_15649_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def F(X, y, b, lam):
+    return np.abs(y - X @ b).sum() + lam * np.abs(b).sum()
+
+
+def rel(a, b):
+    return abs(a - b) / max(1.0, abs(b))
+
+
+def rand_problem(rng, n, p, outliers=True):
+    X = rng.standard_normal((n, p))
+    bt = np.zeros(p)
+    k = min(2, p)
+    bt[rng.choice(p, k, replace=False)] = rng.uniform(-3, 3, k)
+    y = X @ bt + rng.laplace(0, 0.5, n)
+    if outliers:
+        y[rng.choice(n, max(1, n // 10), replace=False)] += 10
+    return X, y
+
+
+# ---------------------------------------------------------------- tiny
+
+def test_tiny_golden_brute_simplex_method_agree():
+    g = json.load(open(os.path.join(HERE, "golden", "tiny_fit.json")))
+    t = synth.tiny()
+    X, y, lam = t["X"].astype(float), t["y"].astype(float), float(t["lam"])
+    fb, bb, nd = oracle.brute_force(X, y, lam)
+    fs, bs = oracle.simplex(X, y, lam)
+    r = oracle.fit_path(X, y, [lam])
+    assert nd == 1
+    assert rel(fb, g["F_star"]) < 1e-12
+    assert rel(fs, fb) < 1e-12
+    assert rel(r["f"][0], fb) < 1e-12
+    assert np.max(np.abs(r["b"][0] - bb)) < 1e-9
+    assert np.max(np.abs(bb - np.array(g["b_star"]))) < 1e-9
+    assert r["status"][0] == oracle.FIT_OK
+    gap, info = oracle.certify(X, y, r["b"][0], lam)
+    assert gap < 1e-9 and info["unique"]
+
+
+def test_simplex_matches_scipy_highs():
+    linprog = pytest.importorskip("scipy.optimize").linprog
+    rng = np.random.default_rng(11)
+    for n, p in [(12, 3), (30, 5), (60, 8)]:
+        X, y = rand_problem(rng, n, p)
+        for lam in [0.05, 1.0, 5.0]:
+            fs, _ = oracle.simplex(X, y, lam)
+            c = np.concatenate([lam * np.ones(2 * p), np.ones(2 * n)])
+            A = np.hstack([X, -X, np.eye(n), -np.eye(n)])
+            res = linprog(c, A_eq=A, b_eq=y, bounds=(0, None), method="highs")
+            assert rel(fs, res.fun) < 1e-9, (n, p, lam, fs, res.fun)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_tiny_brute_equals_simplex_equals_method(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(6, 15))
+    p = int(rng.integers(1, 5))
+    X, y = rand_problem(rng, n, p)
+    lmax = oracle.lambda_max(X, y)
+    for lam in [0.9 * lmax, 0.2 * lmax, 0.02 * lmax, 1e-3 * lmax]:
+        fb, bb, nd = oracle.brute_force(X, y, lam)
+        fs, bs = oracle.simplex(X, y, lam)
+        r = oracle.fit_path(X, y, [lam])
+        assert rel(fs, fb) < 1e-11
+        assert rel(r["f"][0], fb) < 1e-11, (n, p, lam)
+        assert rel(F(X, y, r["b"][0], lam), fb) < 1e-11
+        if nd == 1:
+            assert np.max(np.abs(r["b"][0] - bb)) < 1e-7
+
+
+def test_lambda_path_warm_start_matches_cold_fits():
+    rng = np.random.default_rng(5)
+    X, y = rand_problem(rng, 60, 6)
+    lmax = oracle.lambda_max(X, y)
+    lams = lmax * np.logspace(0, -3, 8)
+    path = oracle.fit_path(X, y, lams)
+    for l, lam in enumerate(lams):
+        fs, _ = oracle.simplex(X, y, lam)
+        assert rel(path["f"][l], fs) < 1e-11
+        cold = oracle.fit_path(X, y, [lam])
+        assert rel(cold["f"][0], fs) < 1e-11
+
+
+def test_medium_method_equals_simplex_and_certificate():
+    rng = np.random.default_rng(7)
+    for n, p in [(200, 8), (400, 16)]:
+        X, y = rand_problem(rng, n, p)
+        lmax = oracle.lambda_max(X, y)
+        lams = lmax * np.logspace(-0.3, -3, 4)
+        path = oracle.fit_path(X, y, lams)
+        for l, lam in enumerate(lams):
+            fs, _ = oracle.simplex(X, y, lam)
+            assert rel(path["f"][l], fs) < 1e-10, (n, p, lam)
+            gap, info = oracle.certify(X, y, path["b"][l], lam)
+            assert gap <= 1e-9 * max(1, path["f"][l])
+            assert path["status"][l] in (oracle.FIT_OK, oracle.FIT_NONUNIQUE)
+
+
+# ---------------------------------------------------------------- axis update
+
+def test_axis_update_is_exact_1d_minimum():
+    rng = np.random.default_rng(3)
+    for trial in range(20):
+        n, p = int(rng.integers(3, 30)), int(rng.integers(1, 5))
+        X, y = rand_problem(rng, n, p)
+        b = rng.standard_normal(p)
+        lam = float(rng.uniform(0, 3))
+        j = int(rng.integers(p))
+        b1, r1, piv = oracle.axis_update(X, y, b, lam, j)
+        # brute force over the 1-D breakpoints of the axis function
+        r0 = y - X @ b
+        nz = X[:, j] != 0
+        cands = np.concatenate([b[j] + r0[nz] / X[nz, j], [0.0]])
+        best = np.inf
+        for t in cands:
+            bt = b.copy()
+            bt[j] = t
+            best = min(best, F(X, y, bt, lam))
+        assert F(X, y, b1, lam) <= best * (1 + 1e-13) + 1e-13
+        assert np.all(np.delete(b1, j) == np.delete(b, j))
+        np.testing.assert_allclose(r1, y - X @ b1, atol=1e-10)
+        if piv >= 0:
+            assert abs(r1[piv]) < 1e-9
+        if piv == -1:
+            assert b1[j] == 0.0
+
+
+def test_p1_closed_form_weighted_median():
+    # p = 1: argmin sum |y_i - x_i b| + lam |b| is the weighted median of
+    # y_i / x_i (weights |x_i|) and 0 (weight lam) -- sorted by hand here.
+    rng = np.random.default_rng(9)
+    for trial in range(10):
+        n = int(rng.integers(5, 40))
+        x = rng.standard_normal((n, 1))
+        y = 2 * x[:, 0] + rng.standard_normal(n)
+        lam = float(rng.uniform(0, 2))
+        z = np.concatenate([y / x[:, 0], [0.0]])
+        w = np.concatenate([np.abs(x[:, 0]), [lam]])
+        o = np.argsort(z)
+        c = np.cumsum(w[o])
+        k = np.searchsorted(c, c[-1] / 2)
+        expect = z[o][k]
+        r = oracle.fit_path(x, y, [lam])
+        assert abs(r["b"][0, 0] - expect) < 1e-12 * max(1, abs(expect))
+
+
+def test_flat_segment_tie_rule_keeps_current_value():
+    # two rows y = 1 and y = 3 with x = 1, lam = 0: every b in [1, 3] is
+    # optimal (a flat minimum, Section 3.5).  The axis update keeps a current
+    # value inside the segment and moves an outside one to the nearer end.
+    X = np.ones((2, 1))
+    y = np.array([1.0, 3.0])
+    for b0, expect in [(2.5, 2.5), (0.0, 1.0), (7.0, 3.0)]:
+        b1, _, _ = oracle.axis_update(X, y, np.array([b0]), 0.0, 0)
+        assert b1[0] == expect
+
+
+# ---------------------------------------------------------------- special cases
+
+def test_lambda_max_gives_zero_and_below_does_not():
+    rng = np.random.default_rng(4)
+    for trial in range(5):
+        X, y = rand_problem(rng, 50, 6)
+        lmax = oracle.lambda_max(X, y)
+        assert abs(lmax - np.abs(X.T @ np.sign(y)).max()) < 1e-12 * lmax
+        r = oracle.fit_path(X, y, [lmax * 1.0001, lmax * 5])
+        assert np.all(r["b"] == 0.0)
+        fs, bs = oracle.simplex(X, y, lmax * 0.95)
+        assert fs < F(X, y, np.zeros(6), lmax * 0.95) - 1e-9
+        r2 = oracle.fit_path(X, y, [lmax * 0.95])
+        assert np.any(r2["b"][0] != 0.0)
+
+
+def test_square_system_tiny_lambda_interpolates():
+    rng = np.random.default_rng(8)
+    for p in [1, 2, 3, 5]:
+        X = rng.standard_normal((p, p)) + 3 * np.eye(p)
+        y = rng.standard_normal(p) * 3
+        lam = 1e-6
+        b = np.linalg.solve(X, y)
+        r = oracle.fit_path(X, y, [lam])
+        # with lam small relative to the rows, the fit interpolates: b = X^-1 y
+        if np.all(np.abs(np.linalg.solve(X.T, lam * np.sign(b))) < 1):
+            np.testing.assert_allclose(r["b"][0], b, rtol=1e-9, atol=1e-9)
+
+
+def test_intercept_only_gives_sample_median():
+    rng = np.random.default_rng(12)
+    for n in [5, 11, 101]:
+        y = rng.standard_normal(n) * 4 + 2
+        X = np.ones((n, 1))
+        o = oracle.default_opts(lambda_min_floor=1e-9)
+        r = oracle.fit_path(X, y, [0.0], opts=o)
+        assert abs(r["b"][0, 0] - np.median(y)) < 1e-9
+
+
+# ---------------------------------------------------------------- invariances
+
+def test_invariances():
+    rng = np.random.default_rng(21)
+    X, y = rand_problem(rng, 80, 5)
+    lam = 0.1 * oracle.lambda_max(X, y)
+    base = oracle.fit_path(X, y, [lam])
+    b0, f0 = base["b"][0], base["f"][0]
+    perm = rng.permutation(80)
+    r = oracle.fit_path(X[perm], y[perm], [lam])
+    assert rel(r["f"][0], f0) < 1e-12
+    np.testing.assert_allclose(r["b"][0], b0, atol=1e-9)
+    cp = rng.permutation(5)
+    r = oracle.fit_path(X[:, cp], y, [lam])
+    np.testing.assert_allclose(r["b"][0], b0[cp], atol=1e-9)
+    # F is positively homogeneous of degree one in (y, b): scaling y by c
+    # with lambda fixed scales the minimiser by c ...
+    c = 3.7
+    r = oracle.fit_path(X, c * y, [lam])
+    np.testing.assert_allclose(r["b"][0], c * b0, atol=1e-8)
+    # ... and scaling (X, y, lambda) together leaves it unchanged
+    r = oracle.fit_path(c * X, c * y, [c * lam])
+    np.testing.assert_allclose(r["b"][0], b0, atol=1e-9)
+    # a duplicated row equals that row with weight 2 (row and target doubled)
+    Xd = np.vstack([X, X[:1]])
+    yd = np.concatenate([y, y[:1]])
+    Xw = X.copy()
+    yw = y.copy()
+    Xw[0] *= 2
+    yw[0] *= 2
+    fd = oracle.simplex(Xd, yd, lam)[0]
+    fw = oracle.simplex(Xw, yw, lam)[0]
+    assert rel(fd, fw) < 1e-11
+    rd = oracle.fit_path(Xd, yd, [lam])
+    assert rel(rd["f"][0], fd) < 1e-11
+
+
+# ---------------------------------------------------------------- certificate
+
+def test_certificate_detects_suboptimal_points():
+    rng = np.random.default_rng(31)
+    X, y = rand_problem(rng, 60, 5)
+    lam = 0.05 * oracle.lambda_max(X, y)
+    fs, bs = oracle.simplex(X, y, lam)
+    gap, info = oracle.certify(X, y, bs, lam)
+    assert gap < 1e-9
+    for trial in range(5):
+        bp = bs + rng.standard_normal(5) * 0.05
+        gp, _ = oracle.certify(X, y, bp, lam)
+        # weak duality: the gap bounds F(b) - F* from above
+        assert gp >= F(X, y, bp, lam) - fs - 1e-9
+        assert gp > 1e-6
+
+
+def test_plain_ccd_stalls_but_method_does_not():
+    # Section 3.3: coordinate descent alone stops at axis-wise minima.
+    rng = np.random.default_rng(41)
+    stalls = 0
+    for trial in range(6):
+        X, y = rand_problem(rng, 100, 8)
+        lam = 0.02 * oracle.lambda_max(X, y)
+        fs, _ = oracle.simplex(X, y, lam)
+        bc, _ = oracle.ccd(X, y, lam)
+        if F(X, y, bc, lam) > fs * (1 + 1e-9):
+            stalls += 1
+        r = oracle.fit_path(X, y, [lam])
+        assert rel(r["f"][0], fs) < 1e-11
+    assert stalls >= 1
+
+
+def test_chop_only_variant_is_not_always_optimal_but_never_worse():
+    rng = np.random.default_rng(43)
+    for trial in range(4):
+        X, y = rand_problem(rng, 60, 6)
+        lam = 0.05 * oracle.lambda_max(X, y)
+        bc, _ = oracle.ccd(X, y, lam)
+        o = oracle.default_opts(polish=0)
+        r = oracle.fit_path(X, y, [lam], opts=o)
+        assert r["f"][0] <= F(X, y, bc, lam) * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------- gradient
+
+def test_active_set_gradient_matches_finite_differences():
+    rng = np.random.default_rng(51)
+    n, nv, p = 60, 20, 4
+    Xa = rng.standard_normal((n + nv, p))
+    bt = np.array([1.5, 0, -2, 0.0])
+    ya = Xa @ bt + rng.laplace(0, 1, n + nv)
+    X, y, Xv, yv = Xa[:n], ya[:n], Xa[n:], ya[n:]
+    lam = 0.1 * oracle.lambda_max(X, y)
+
+    def loss(X_, y_, lam_):
+        r = oracle.fit_path(X_, y_, [lam_])
+        return np.abs(yv - Xv @ r["b"][0]).sum(), r
+
+    L0, r0 = loss(X, y, lam)
+    g = oracle.grad(X, y, r0["b"][0], r0["basis"][0], Xv, yv)
+    assert g["ok"]
+    h = 1e-3
+    checked = 0
+    # y entries
+    for i in range(n):
+        yp, ym = y.copy(), y.copy()
+        yp[i] += h
+        ym[i] -= h
+        Lp, rp = loss(X, yp, lam)
+        Lm, rm = loss(X, ym, lam)
+        if sorted(rp["basis"][0]) != sorted(r0["basis"][0]) or \
+           sorted(rm["basis"][0]) != sorted(r0["basis"][0]):
+            continue  # not a generic point: the vertex changes within h
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - g["gy"][i]) <= 1e-3 * max(1, abs(fd)), (i, fd, g["gy"][i])
+        checked += 1
+    # X entries of basis rows
+    for i in set(int(c) for c in r0["basis"][0] if c >= 0):
+        for j in range(p):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[i, j] += h
+            Xm[i, j] -= h
+            Lp, rp = loss(Xp, y, lam)
+            Lm, rm = loss(Xm, y, lam)
+            if sorted(rp["basis"][0]) != sorted(r0["basis"][0]) or \
+               sorted(rm["basis"][0]) != sorted(r0["basis"][0]):
+                continue
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - g["gX"][i, j]) <= 1e-3 * max(1, abs(fd))
+            checked += 1
+    # lambda: zero at a generic vertex
+    Lp, _ = loss(X, y, lam + h)
+    Lm, _ = loss(X, y, lam - h)
+    assert abs((Lp - Lm) / (2 * h) - g["glam"]) < 1e-6
+    # validation rows (direct terms)
+    for v in range(3):
+        yvp = yv.copy()
+        yvp[v] += h
+        fd = (np.abs(yvp - Xv @ r0["b"][0]).sum() - L0) / h
+        assert abs(fd - g["gyv"][v]) < 1e-6
+    assert checked >= n // 2
+
+
+# ---------------------------------------------------------------- batch API
+
+def test_fit_batch_matches_single_fits():
+    batch = synth.batched_like(6, 30, 80, 2, 6, R=120, P=8, seed=5)
+    lm = np.array([oracle.lambda_max(*oracle.problem(batch, q)) for q in range(6)])
+    lams = lm[:, None] * np.logspace(0, -2, 3)[None, :]
+    res = oracle.fit_batch(batch, lams, nthreads=2)
+    for q in range(6):
+        Xq, yq = oracle.problem(batch, q)
+        r = oracle.fit_path(Xq, yq, lams[q])
+        np.testing.assert_array_equal(res["b"][q, :, :Xq.shape[1]], r["b"])
+        np.testing.assert_array_equal(res["f"][q], r["f"])
+
+
+def test_bad_lambda_status():
+    rng = np.random.default_rng(2)
+    X, y = rand_problem(rng, 20, 3)
+    r = oracle.fit_path(X, y, [1.0, -1.0, np.nan, 0.5])
+    assert list(r["status"][[1, 2]]) == [oracle.FIT_BAD_INPUT] * 2
+    assert np.all(r["b"][1:3] == 0)
+    assert r["status"][3] in (0, oracle.FIT_NONUNIQUE)
