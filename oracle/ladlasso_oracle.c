@@ -96,7 +96,7 @@ void orc_default_opts(orc_opts* o) {
   o->chop_tol = 1e-3;
   o->chop_max_probes = 12;
   o->chop_max_extend = 20;
-  o->probe_max_sweeps = 8;
+  o->probe_max_sweeps = 4;
   o->polish = 1;
   o->max_pivots = 2000;
   o->tol_opt = 1e-10;
