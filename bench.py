@@ -1,0 +1,355 @@
+"""Benchmark: batched LAD-LASSO fits on one GB300 (or N, one process each).
+
+Workload (default): 4096 row-subset problems of a shared 2000 x 32 N(0,1)
+matrix, n ~ U{50..2000}, p ~ U{4..32}, 16 lambdas from lambda_max down to
+1e-3 lambda_max with warm starts.  One step = lambda_max + lambda path +
+the full fit (coordinate descent, ternary chop, exact polish) of every
+(problem, lambda) pair, all in this library's kernels.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead (bounded samples of the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2510_15649_gb300 import synth  # noqa: E402
+
+WORKLOAD = "batched 4096 problems, shared X 2000x32, n~U[50,2000], p~U[4,32], L=16 (1e-3 path)"
+METRIC = "LAD-LASSO fits/s (certified, rel. obj err <= 1e-5 vs FP64 oracle)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--problems", type=int, default=4096)
+    ap.add_argument("--L", type=int, default=16)
+    ap.add_argument("--parity-sample", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-thread", action="store_true", help="skip the thread-per-fit comparison")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    """FP64 CPU oracle on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    batch = synth.batched(B=args.problems, seed=1)
+    cores = os.cpu_count() or 1
+    per_step = max(4, min(64, cores * 2))
+    lm = []
+    for q in range(per_step * (args.steps + args.warmup)):
+        lm.append(oracle.lambda_max(*oracle.problem(batch, q % args.problems)))
+    times = []
+    for s in range(args.warmup + args.steps):
+        qs = np.arange(s * per_step, (s + 1) * per_step) % args.problems
+        lams = np.array(lm[s * per_step:(s + 1) * per_step])[:, None] * \
+            1e-3 ** (np.arange(args.L) / (args.L - 1))[None, :]
+        lam_full = np.zeros((args.problems, args.L))
+        lam_full[qs] = lams
+        t0 = time.perf_counter()
+        r = oracle.fit_batch(batch, lam_full, problems=qs, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+        used = r["threads"]
+    fits = per_step * args.L
+    v = fits / statistics.median(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "fits/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{per_step} problems x {args.L} lambdas per step"},
+            "cpu_baseline": {"value": v, "unit": "fits/s", "cores": used, "kind": "oracle",
+                             "sample": f"{per_step} problems x {args.L} lambdas per step"},
+            "e2e": {"value": v, "unit": "fits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def row_updates(batch, counters, B):
+    """Row-updates (one row's part in one 1-D weighted-median step) per fit:
+    CCD/probe sweeps x p x n + polish steps x n (approximate: restricted
+    sweeps skip one axis)."""
+    n = np.diff(batch["offsets"])[:B].astype(np.float64)
+    p = batch["p"][:B].astype(np.float64)
+    sw = counters[:, :, 0].astype(np.float64)
+    pv = counters[:, :, 2].astype(np.float64)
+    return float(np.sum((sw * p[:, None] + pv) * n[:, None]))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2510_15649_gb300 import build as _b
+    if rank == 0:
+        _b.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2510_15649_gb300 import ladlasso as ll
+
+    B, L = args.problems, args.L
+    batch = synth.batched(B=B, seed=1 + 1000 * rank)  # weak scaling: one batch per rank
+    dev = torch.device("cuda", local)
+    pr = ll.Problems.from_numpy(batch, device=dev)
+    ws = ll.workspace(pr, L)
+    out = dict(b=torch.empty((B, L, pr.P), device=dev), obj=torch.empty((B, L), device=dev),
+               status=torch.empty((B, L), dtype=torch.int32, device=dev),
+               counters=torch.empty((B, L, 4), dtype=torch.int32, device=dev))
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        lm = ll.lambda_max(pr, ws)
+        lam = ll.lambda_path(lm, L, 1e-3)
+        ll.fit(pr, lam, ws=ws, out=out)
+        return lam
+
+    launches_per_step = 5  # 2 offset checks, lambda_max, lambda_path, fit
+    for _ in range(args.warmup):
+        lam = step()
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)  # L2 flush between timed steps (outside the events)
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lam = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    t_step = statistics.median(times)
+    if dist is not None:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    st = out["status"].cpu().numpy()
+    cnt = out["counters"].cpu().numpy()
+    certified = int(np.sum((st & 3) == 0))
+    fits = B * L
+    value_rank = certified / t_step
+    total_fits = fits * world
+    value = (certified * world) / t_step
+
+    # kernel-only time of the fit launch (events on the launching stream)
+    lam_fixed = lam.clone()
+    kt = []
+    for _ in range(3):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ll.fit(pr, lam_fixed, ws=ws, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kt.append(e0.elapsed_time(e1) / 1e3)
+    t_fit = statistics.median(kt)
+
+    # end to end through the public API with pinned host buffers
+    hX = torch.as_tensor(batch["X"]).pin_memory()
+    hy = torch.as_tensor(batch["y"]).pin_memory()
+    hri = torch.as_tensor(batch["row_idx"]).pin_memory()
+    hoff = torch.as_tensor(batch["offsets"]).pin_memory()
+    hp = torch.as_tensor(batch["p"]).pin_memory()
+    hb = torch.empty((B, L, pr.P)).pin_memory()
+    hobj = torch.empty((B, L)).pin_memory()
+    hst = torch.empty((B, L), dtype=torch.int32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in (hX, hy, hri, hoff, hp))
+    d2h = sum(t.numel() * t.element_size() for t in (hb, hobj, hst))
+    et = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p2 = ll.Problems(X=hX.to(dev, non_blocking=True), y=hy.to(dev, non_blocking=True),
+                         offsets=hoff.to(dev, non_blocking=True),
+                         row_idx=hri.to(dev, non_blocking=True), p=hp.to(dev, non_blocking=True),
+                         P=pr.P, n_max=pr.n_max)
+        lm = ll.lambda_max(p2, ws)
+        lam2 = ll.lambda_path(lm, L, 1e-3)
+        o2 = ll.fit(p2, lam2, ws=ws)
+        hb.copy_(o2["b"], non_blocking=True)
+        hobj.copy_(o2["obj"], non_blocking=True)
+        hst.copy_(o2["status"], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        et.append(e0.elapsed_time(e1) / 1e3)
+    t_e2e = statistics.median(et)
+
+    line = {"metric": METRIC, "value": value, "unit": "fits/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "problems_per_gpu": B, "lambdas": L,
+                       "fits_per_gpu": fits, "l2": "flushed between timed steps (256 MB write)"},
+            "certified_fraction": certified / fits,
+            "gpu_launches": launches_per_step * args.steps,
+            "e2e": {"value": certified * world / t_e2e, "unit": "fits/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+
+    # parity on a sample of fits against the FP64 oracle
+    if rank == 0 and args.parity_sample > 0:
+        import oracle
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        oracle.build()
+        bh = out["b"].cpu().numpy()
+        lh = lam.cpu().numpy()
+        rng = np.random.default_rng(123)
+        qs = sorted(rng.choice(B, args.parity_sample, replace=False).tolist())
+        worst = 0.0
+        fails = 0
+        for q in qs:
+            X, y = oracle.problem(batch, q)
+            ref = oracle.fit_path(X, y, lh[q].astype(np.float64))
+            for l in range(L):
+                fg = oracle.objective(X, y, bh[q, l, :X.shape[1]].astype(np.float64), float(lh[q, l]))
+                e = abs(fg - ref["f"][l]) / max(1.0, ref["f"][l])
+                worst = max(worst, e)
+                fails += e > 1e-5
+        line["parity_sample"] = {"problems": qs, "fits": len(qs) * L, "worst_rel_obj": worst,
+                                 "fails": int(fails)}
+
+    # roofline of the fit kernel: issue-bound selection work
+    ru = row_updates(batch, cnt, B)
+    clk_s = clk.summary()
+    mhz = clk_s.get("sm_mhz") or 1900.0
+    flops_per_ru = 6.0  # key (div+add), weight accumulate/compare, residual FMA
+    achieved = flops_per_ru * ru / t_fit / 1e12
+    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x clock
+    line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "fit_block_kernel", "kernel_ms": 1e3 * t_fit,
+                        "row_updates_per_launch": ru}
+    line["clocks"] = clk_s
+
+    # thread-per-fit comparison on the same inputs
+    if not args.no_thread and rank == 0:
+        try:
+            tt = []
+            for _ in range(2):
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                o3 = ll.fit(pr, lam_fixed, ws=ws, per_thread=True)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tt.append(e0.elapsed_time(e1) / 1e3)
+            s3 = o3["status"].cpu().numpy()
+            line["thread_per_fit"] = {"fits_per_s": int(np.sum((s3 & 3) == 0)) / min(tt),
+                                      "kernel_ms": 1e3 * min(tt)}
+            line["speedup_vs_thread_per_fit"] = (certified / t_fit) / line["thread_per_fit"]["fits_per_s"]
+        except Exception as ex:  # report, do not fail the bench line
+            line["thread_per_fit"] = {"error": str(ex)}
+
+    # CPU oracle baseline on a bounded sample
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        nq = max(8, min(48, 2 * cores))
+        lh = lam.cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        r = oracle.fit_batch(batch, lh, problems=np.arange(nq), nthreads=cores)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": nq * L / dt, "unit": "fits/s", "cores": r["threads"],
+                                "kind": "oracle", "sample": f"problems 0..{nq - 1} x {L} lambdas"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,101 @@
+// Small kernels around the fit: offset validation, lambda_max, lambda path.
+#include "common.cuh"
+
+namespace ll {
+namespace {
+
+// ctrl[1] = 1 if offsets are not non-decreasing from 0 to total_rows.
+__global__ void validate_offsets_kernel(const int64_t* offsets, int B, int64_t total_rows,
+                                        int* ctrl) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q <= B; q += gridDim.x * blockDim.x) {
+    int64_t o = offsets[q];
+    bool bad = o < 0 || o > total_rows || (q > 0 && offsets[q - 1] > o) ||
+               (q == B && o != total_rows);
+    if (bad) atomicOr(ctrl + 1, 1);
+  }
+}
+
+// lambda_max per problem: max_j |sum_i x_ij sign(y_i)|.  One block per
+// problem (grid-stride over problems); threads stride over rows, one
+// column at a time, fixed-order reductions.
+__global__ void lambda_max_kernel(FitArgs a, float* lmax) {
+  __shared__ float red[32];
+  __shared__ int bad_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x / 32;
+  const int* ctrl = a.queue;
+  for (int q = blockIdx.x; q < a.B; q += gridDim.x) {
+    int64_t o0 = a.offsets[q];
+    int64_t o1 = a.offsets[q + 1];
+    int p = a.p ? a.p[q] : a.P;
+    bool ok = ctrl[1] == 0 && o0 >= 0 && o1 >= o0 && o1 <= a.total_rows &&
+              (o1 - o0) <= (int64_t)a.n_max && p >= 1 && p <= a.P;
+    if (tid == 0) bad_s = ok ? 0 : 1;
+    __syncthreads();
+    int n = ok ? (int)(o1 - o0) : 0;
+    float best = 0.f;
+    for (int c = 0; c < p && ok; ++c) {
+      float s = 0.f;
+      int bad = 0;
+      for (int i = tid; i < n; i += blockDim.x) {
+        int64_t row = a.row_idx ? (int64_t)a.row_idx[o0 + i] : o0 + i;
+        if (row < 0 || row >= a.rows_X) { bad = 1; continue; }
+        float yv = a.y[o0 + i];
+        float x = a.X[row * a.ldX + c];
+        if (!isfinite(x) || !isfinite(yv)) bad = 1;
+        s += x * fsign(yv);
+      }
+      if (bad) atomicOr(&bad_s, 1);
+      s = warp_sum(s);
+      __syncthreads();
+      if (lane == 0) red[warp] = s;
+      __syncthreads();
+      float t = 0.f;
+      for (int w = 0; w < nw; ++w) t += red[w];
+      best = fmaxf(best, fabsf(t));
+    }
+    __syncthreads();
+    if (tid == 0) lmax[q] = bad_s ? NAN : best;
+    __syncthreads();
+  }
+}
+
+__global__ void lambda_path_kernel(const float* lmax, int B, int L, float ratio, float* lam) {
+  int64_t total = (int64_t)B * L;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int q = (int)(e / L), l = (int)(e % L);
+    float t = L > 1 ? (float)l / (float)(L - 1) : 0.f;
+    lam[e] = lmax[q] * powf(ratio, t);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t total_rows, int* ctrl,
+                                    cudaStream_t st) {
+  int threads = 256;
+  int blocks = (B + 1 + threads - 1) / threads;
+  if (blocks > 4096) blocks = 4096;
+  validate_offsets_kernel<<<blocks, threads, 0, st>>>(offsets, B, total_rows, ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lambda_max(const FitArgs& a, float* lmax, cudaStream_t st, int num_sms) {
+  int grid = a.B < num_sms * 8 ? a.B : num_sms * 8;
+  if (grid < 1) return cudaSuccess;
+  lambda_max_kernel<<<grid, 256, 0, st>>>(a, lmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lambda_path(const float* lmax, int B, int L, float ratio, float* lam,
+                               cudaStream_t st) {
+  int64_t total = (int64_t)B * L;
+  if (total == 0) return cudaSuccess;
+  int threads = 256;
+  int64_t blocks = (total + threads - 1) / threads;
+  if (blocks > 65535) blocks = 65535;
+  lambda_path_kernel<<<(int)blocks, threads, 0, st>>>(lmax, B, L, ratio, lam);
+  return cudaGetLastError();
+}
+
+}  // namespace ll

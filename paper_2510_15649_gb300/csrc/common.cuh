@@ -1,0 +1,109 @@
+// Shared device-side definitions for the batched LAD-LASSO library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ladlasso.h"
+
+namespace ll {
+
+constexpr int kFitOk = LADLASSO_FIT_OK;
+constexpr int kFitMaxIters = LADLASSO_FIT_MAX_ITERS;
+constexpr int kFitBadInput = LADLASSO_FIT_BAD_INPUT;
+constexpr int kFitNonunique = LADLASSO_FIT_NONUNIQUE;
+
+// Breakpoint owner codes: rows are >= 0; coordinate j is -(j+1);
+// kNone marks a result strictly inside a flat segment.
+constexpr int kNone = -0x40000000;
+__host__ __device__ inline int coord_code(int j) { return -j - 1; }
+
+constexpr int kMaxP = 256;  // largest supported P_cols
+
+struct Opts {
+  float tol_move;
+  int max_sweeps;
+  int chop;
+  float chop_bracket;
+  float chop_tol;
+  int chop_max_probes;
+  int chop_max_extend;
+  int probe_max_sweeps;
+  int polish;
+  int max_pivots;
+  float tol_opt;
+  float lambda_min_floor;
+};
+
+// Everything a fit kernel needs; passed by value.
+struct FitArgs {
+  const float* X;
+  const float* y;
+  const int32_t* row_idx;
+  const int64_t* offsets;
+  const int32_t* p;
+  const float* lambdas;
+  const float* b_init;
+  float* b_out;
+  float* obj_out;
+  int32_t* status;
+  int32_t* basis_out;
+  int32_t* counters;
+  float* Xg;        // workspace: gathered column-major designs
+  int* queue;       // workspace: work counter
+  unsigned char* scratch;  // workspace: per-fit scratch (thread-per-fit kernel)
+  int B, P, L, n_max;
+  int64_t ldX, rows_X, total_rows;
+  int P4;           // P rounded up to a multiple of 4
+  Opts o;
+};
+
+// Workspace layout (bytes, 256-aligned sections):
+//   [0, 256)            control words (work counters)
+//   Xg                  (total_rows + 4 B) * P4 floats: problem q's column j
+//                       starts at xg_base(q) + j * ld(n_q), ld = round_up(n,4)
+//   thread scratch      per-slot and per-problem scratch for the
+//                       thread-per-fit kernel
+__host__ __device__ inline int64_t xg_base(int64_t off_q, int q, int P4) {
+  return (off_q + 4 * (int64_t)q) * P4;
+}
+__host__ __device__ inline int64_t xg_ld(int n) { return ((int64_t)n + 3) & ~(int64_t)3; }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float fsign(float v) { return (float)((v > 0.f) - (v < 0.f)); }
+
+// Validate problem q; on success fill off0, n, p.  Returns false on bad input.
+__device__ inline bool problem_ok(const FitArgs& a, int q, int64_t& off0, int& n, int& p,
+                                  int n_cap) {
+  if (a.queue[1] != 0) return false;  // offsets failed the monotonicity check
+  off0 = a.offsets[q];
+  int64_t off1 = a.offsets[q + 1];
+  if (off0 < 0 || off1 < off0 || off1 > a.total_rows) return false;
+  int64_t nn = off1 - off0;
+  if (nn > (int64_t)a.n_max || nn > (int64_t)n_cap) return false;
+  n = (int)nn;
+  p = a.p ? a.p[q] : a.P;
+  if (p < 1 || p > a.P) return false;
+  return true;
+}
+
+}  // namespace ll

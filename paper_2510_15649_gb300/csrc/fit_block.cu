@@ -1,0 +1,1075 @@
+// Block-per-fit kernel: one thread block of G threads owns one LAD-LASSO fit
+// at a time and takes problems from a device work queue (persistent grid).
+//
+// Per fit (rows i < n distributed cyclically: thread t owns i = t + k*G):
+//   registers  r[K]   residual y - X b of the thread's rows
+//              xw[K]  the current column x_ij (CCD) or edge slope v_i (polish)
+//   shared     breakpoint keys/weights of the current 1-D problem (selection
+//              buffer), the coefficient vector and the p x p basis algebra
+//   global     the problem's design gathered column-major (workspace), so a
+//              column read is one coalesced sweep
+//
+// Method, per lambda of the path (paper: Sections 3.3-3.5):
+//   1. cyclical coordinate descent, each axis step the exact 1-D minimiser:
+//      the weighted median of z_i = b_j + r_i / x_ij (weights |x_ij|) and 0
+//      (weight lambda), found by sample-bracketed selection, not a sort;
+//   2. if the CCD fixed point is not optimal: ternary chop along the axis
+//      of largest |b_k|, each probe a CCD restricted to the other axes,
+//      with range extension; then CCD again;
+//   3. exact polish: edge line searches between vertices (each again a
+//      weighted median) until the optimality multipliers certify the vertex.
+#include "common.cuh"
+
+namespace ll {
+namespace {
+
+constexpr float kInf = INFINITY;
+constexpr int kSampM = 3;  // sample-bracket half-width (in samples)
+constexpr int kU = 4;      // elements per thread per compaction chunk
+
+// Uniform per-block state, resident in shared memory.
+struct St {
+  // arrays carved from dynamic shared memory
+  float* rr;                           // residual [cap]
+  float* ck; float* cw; int* cid;     // selection buffer [cap]
+  float* bv; float* bbest; float* dv; float* mu; float* tv; float* hv;  // [P]
+  float* Bm;                           // [P*P]
+  float* red2;                         // [W*P]
+  int* code; int* phan; int* piv; int* perm; int* pcol;  // [P]
+  unsigned* mask;                      // basis-row bitmap [maskw]
+  float* redf; int* redi;              // reductions [W*16]
+  float* sampk; float* sampw;          // [32]
+  int cap, maskw;
+  // the problem
+  const FitArgs* a;
+  const float* Xq;   // gathered design (column j at Xq + j*ld)
+  const float* yq;   // targets
+  int n, p, ld, nspec;
+  float lam;
+  // broadcast slots
+  float lo, hi, acc, wpart, half, zstar, above;
+  int part, m, owner, q, flag, iter, first;
+};
+
+template <int G>
+__device__ __forceinline__ void gsync() {
+  if (G == 32) __syncwarp(); else __syncthreads();
+}
+
+// Deterministic group reductions: warp butterflies, then warps combined in a
+// fixed order.  NS float sums, NM float mins, NI int sums, NJ int mins.
+template <int G, int NS, int NM, int NI, int NJ>
+__device__ __forceinline__ void reduce(St& s, float (&fs)[NS], float (&mn)[NM], int (&si)[NI],
+                                       int (&mi)[NJ]) {
+  constexpr int W = G / 32;
+#pragma unroll
+  for (int e = 0; e < NS; ++e) fs[e] = warp_sum(fs[e]);
+#pragma unroll
+  for (int e = 0; e < NM; ++e) mn[e] = warp_min(mn[e]);
+#pragma unroll
+  for (int e = 0; e < NI; ++e) si[e] = warp_sum_i(si[e]);
+#pragma unroll
+  for (int e = 0; e < NJ; ++e) {
+    int v = mi[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    mi[e] = v;
+  }
+  if (W == 1) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int e = 0; e < NS; ++e) s.redf[warp * 16 + e] = fs[e];
+#pragma unroll
+    for (int e = 0; e < NM; ++e) s.redf[warp * 16 + NS + e] = mn[e];
+#pragma unroll
+    for (int e = 0; e < NI; ++e) s.redi[warp * 16 + e] = si[e];
+#pragma unroll
+    for (int e = 0; e < NJ; ++e) s.redi[warp * 16 + NI + e] = mi[e];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < NS; ++e) {
+    float t = 0.f;
+    for (int w = 0; w < W; ++w) t += s.redf[w * 16 + e];
+    fs[e] = t;
+  }
+#pragma unroll
+  for (int e = 0; e < NM; ++e) {
+    float t = kInf;
+    for (int w = 0; w < W; ++w) t = fminf(t, s.redf[w * 16 + NS + e]);
+    mn[e] = t;
+  }
+#pragma unroll
+  for (int e = 0; e < NI; ++e) {
+    int t = 0;
+    for (int w = 0; w < W; ++w) t += s.redi[w * 16 + e];
+    si[e] = t;
+  }
+#pragma unroll
+  for (int e = 0; e < NJ; ++e) {
+    int t = INT32_MAX;
+    for (int w = 0; w < W; ++w) t = min(t, s.redi[w * 16 + NI + e]);
+    mi[e] = t;
+  }
+}
+
+template <int G>
+__device__ __forceinline__ float gsum2(St& s, float a, float b, float& bsum) {
+  float f[2] = {a, b}, m[1] = {kInf};
+  int si[1] = {0}, mi[1] = {0};
+  reduce<G, 2, 1, 1, 1>(s, f, m, si, mi);
+  bsum = f[1];
+  return f[0];
+}
+
+// Exclusive scan of per-thread counts in thread order.
+template <int G>
+__device__ __forceinline__ int gscan(St& s, int cnt, int& total) {
+  constexpr int W = G / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  int wtot = __shfl_sync(0xffffffffu, inc, 31);
+  if (W == 1) { total = wtot; return inc - cnt; }
+  __syncthreads();
+  if (lane == 0) s.redi[warp * 16 + 15] = wtot;
+  __syncthreads();
+  int base = 0, tot = 0;
+  for (int w = 0; w < W; ++w) {
+    int c = s.redi[w * 16 + 15];
+    if (w < warp) base += c;
+    tot += c;
+  }
+  total = tot;
+  return base + inc - cnt;
+}
+
+// ------------------------------------------------------------------ selection
+
+// Warp 0: sort 32 (key, weight) samples and bracket the sample position
+// where the cumulative weight reaches `frac` of the sample total.
+__device__ __noinline__ void bracket_from_samples(St& s, int ns, float frac) {
+  const int lane = threadIdx.x & 31;
+  float k = lane < ns ? s.sampk[lane] : kInf;
+  float w = lane < ns ? s.sampw[lane] : 0.f;
+  int id = lane;
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      float ok = __shfl_xor_sync(0xffffffffu, k, stride);
+      float ow = __shfl_xor_sync(0xffffffffu, w, stride);
+      int oi = __shfl_xor_sync(0xffffffffu, id, stride);
+      bool up = (lane & size) == 0;
+      bool lower = (lane & stride) == 0;
+      bool other_less = ok < k || (ok == k && oi < id);
+      bool take = (lower == up) ? other_less : !other_less;
+      if (take) { k = ok; w = ow; id = oi; }
+    }
+  }
+  float cum = w;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    float t = __shfl_up_sync(0xffffffffu, cum, o);
+    if (lane >= o) cum += t;
+  }
+  float tot = __shfl_sync(0xffffffffu, cum, 31);
+  unsigned hit = __ballot_sync(0xffffffffu, cum >= frac * tot);
+  int a = hit ? __ffs(hit) - 1 : 31;
+  int ilo = a - kSampM, ihi = a + kSampM;
+  float lo = __shfl_sync(0xffffffffu, k, max(ilo, 0));
+  float hi = __shfl_sync(0xffffffffu, k, min(ihi, 31));
+  if (lane == 0) {
+    s.lo = ilo < 0 ? -kInf : lo;
+    s.hi = ihi > 31 ? kInf : hi;
+  }
+  __syncwarp();
+}
+
+// Crossing at the group of keys equal to z with cumulative weight `cum`
+// after it.  Exactly half: every t in [z, next] minimises; keep `cur`
+// inside, else take the nearer end (the far end gets no owner: the basis
+// builder then completes with coordinate hyperplanes).
+__device__ __forceinline__ void finalize(St& s, float z, int owner, float cum, float next,
+                                         float cur) {
+  s.flag = 1;
+  s.zstar = z;
+  s.owner = owner;
+  if (cum == s.half && next < kInf) {
+    if (cur > z && cur < next) { s.zstar = cur; s.owner = kNone; }
+    else if (cur >= next) { s.zstar = next; s.owner = kNone; }
+  }
+}
+
+// Thread 0: where does the cumulative weight reach half?
+__device__ __forceinline__ void decide(St& s, const float (&w5)[5], const float (&mn)[2],
+                                       const int (&si)[3], const int (&mi)[2], float cur) {
+  float c[5];
+  c[0] = s.acc + w5[0];
+  c[1] = c[0] + w5[1];
+  c[2] = c[1] + w5[2];
+  c[3] = c[2] + w5[3];
+  c[4] = c[3] + w5[4];
+  // first group reaching half; rounding can leave every cumulative just
+  // below it, then the last group with positive weight takes the crossing
+  int g = 0;
+  while (g < 4 && !(s.half <= c[g])) ++g;
+  while (g > 0 && !(w5[g] > 0.f)) --g;
+  s.flag = 0;
+  if (g == 0) {
+    s.part = 0; s.m = si[0]; s.wpart = w5[0]; s.above = s.lo;
+  } else if (g == 1) {
+    finalize(s, s.lo, mi[0], c[1], fminf(mn[0], s.above), cur);
+  } else if (g == 2) {
+    s.part = 2; s.m = si[1]; s.wpart = w5[2]; s.acc = c[1]; s.above = s.hi;
+  } else if (g == 3) {
+    finalize(s, s.hi, mi[1], c[3], fminf(mn[1], s.above), cur);
+  } else {
+    s.part = 4; s.m = si[2]; s.wpart = w5[4]; s.acc = c[3];
+  }
+}
+
+__device__ __forceinline__ bool in_part(float kk, float lo, float hi, int part) {
+  return part == 0 ? kk < lo : (part == 2 ? (kk > lo && kk < hi) : kk > hi);
+}
+
+// Weighted median of the m elements of the selection buffer: ck (keys), cw
+// (weights), ids implicit (= position) for positions < s.n on the first
+// level, else cid.  Smallest key whose cumulative weight reaches half the
+// total; ties between equal keys: the lowest id among positive weights.
+// Each level brackets the target with 32 samples, classifies every element
+// into (<lo, ==lo, (lo,hi), ==hi, >hi) with fixed-order weight sums, and
+// compacts the part holding the target in place; <= 32 elements are sorted
+// by one warp.  Result in s.zstar / s.owner (kNone: no breakpoint owner).
+template <int G>
+__device__ __noinline__ void select(St& s, int m0, float cur) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float ws = 0.f;
+  for (int e = tid; e < m0; e += G) ws += s.cw[e];
+  float dummy;
+  float W = gsum2<G>(s, ws, 0.f, dummy);
+  if (!(W > 0.f)) {
+    gsync<G>();
+    if (tid == 0) { s.zstar = cur; s.owner = kNone; }
+    gsync<G>();
+    return;
+  }
+  if (tid == 0) {
+    s.half = 0.5f * W; s.acc = 0.f; s.above = kInf; s.wpart = W; s.m = m0; s.first = 1;
+    s.flag = 0;
+  }
+  gsync<G>();
+  const int n = s.n;
+  for (;;) {
+    const int m = s.m;
+    const int first = s.first;
+    if (m <= 32) break;
+    if (warp == 0) {
+      int e = (int)(((int64_t)lane * m) / 32);
+      s.sampk[lane] = s.ck[e];
+      s.sampw[lane] = s.cw[e];
+      __syncwarp();
+      float wp = s.wpart;
+      float frac = wp > 0.f ? (s.half - s.acc) / wp : 0.5f;
+      bracket_from_samples(s, 32, fminf(fmaxf(frac, 0.f), 1.f));
+    }
+    gsync<G>();
+    const float lo = s.lo, hi = s.hi;
+    float w5[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, mn[2] = {kInf, kInf};
+    int si[3] = {0, 0, 0}, mi[2] = {INT32_MAX, INT32_MAX};
+    for (int e = tid; e < m; e += G) {
+      float kk = s.ck[e], ww = s.cw[e];
+      int id = (first && e < n) ? e : s.cid[e];
+      if (kk < lo) { w5[0] += ww; si[0] += 1; }
+      else if (kk == lo) { w5[1] += ww; if (ww > 0.f) mi[0] = min(mi[0], id); }
+      else if (kk < hi) { w5[2] += ww; si[1] += 1; }
+      else if (kk == hi) { w5[3] += ww; if (ww > 0.f) mi[1] = min(mi[1], id); }
+      else { w5[4] += ww; si[2] += 1; }
+      if (kk > lo) mn[0] = fminf(mn[0], kk);
+      if (kk > hi) mn[1] = fminf(mn[1], kk);
+    }
+    reduce<G, 5, 2, 3, 2>(s, w5, mn, si, mi);
+    if (tid == 0) decide(s, w5, mn, si, mi, cur);
+    gsync<G>();
+    if (s.flag) break;
+    const int part = s.part;
+    // in-place compaction in chunks of G*kU: all reads of a chunk happen
+    // before its scan barrier; writes land at positions already read
+    int base = 0;
+    for (int c0 = 0; c0 < m; c0 += G * kU) {
+      float bk[kU], bw[kU];
+      int bi[kU];
+      int cnt = 0;
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        int e = c0 + u * G + tid;
+        bool in = false;
+        if (e < m) {
+          bk[u] = s.ck[e]; bw[u] = s.cw[e];
+          bi[u] = (first && e < n) ? e : s.cid[e];
+          in = in_part(bk[u], lo, hi, part);
+        }
+        if (!in) bk[u] = NAN;  // marks "not kept"
+        cnt += in;
+      }
+      int total;
+      int pos = base + gscan<G>(s, cnt, total);
+      if (G == 32) __syncwarp();
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        if (bk[u] == bk[u]) { s.ck[pos] = bk[u]; s.cw[pos] = bw[u]; s.cid[pos] = bi[u]; ++pos; }
+      }
+      base += total;
+      gsync<G>();
+    }
+    if (tid == 0) s.first = 0;
+    gsync<G>();
+  }
+  if (!s.flag && warp == 0) {
+    // at most 32 candidates: one warp sorts by (key, id) and scans
+    const int m = s.m;
+    const int first = s.first;
+    float k = lane < m ? s.ck[lane] : kInf;
+    float w = lane < m ? s.cw[lane] : 0.f;
+    int id = lane < m ? ((first && lane < n) ? lane : s.cid[lane]) : INT32_MAX - lane;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        float ok = __shfl_xor_sync(0xffffffffu, k, stride);
+        float ow = __shfl_xor_sync(0xffffffffu, w, stride);
+        int oi = __shfl_xor_sync(0xffffffffu, id, stride);
+        bool up = (lane & size) == 0;
+        bool lower = (lane & stride) == 0;
+        bool other_less = ok < k || (ok == k && oi < id);
+        bool take = (lower == up) ? other_less : !other_less;
+        if (take) { k = ok; w = ow; id = oi; }
+      }
+    }
+    float cum = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      float t = __shfl_up_sync(0xffffffffu, cum, o);
+      if (lane >= o) cum += t;
+    }
+    float acc = s.acc, half = s.half;
+    unsigned hit = __ballot_sync(0xffffffffu, lane < m && acc + cum >= half);
+    unsigned posw = __ballot_sync(0xffffffffu, lane < m && w > 0.f);
+    int c = hit ? __ffs(hit) - 1 : (posw ? 31 - __clz(posw) : 0);
+    float z = __shfl_sync(0xffffffffu, k, c);
+    unsigned eq = __ballot_sync(0xffffffffu, lane < m && k == z);
+    unsigned eqw = __ballot_sync(0xffffffffu, lane < m && k == z && w > 0.f);
+    int last = 31 - __clz(eq);
+    int own_lane = eqw ? __ffs(eqw) - 1 : c;
+    int own = __shfl_sync(0xffffffffu, id, own_lane);
+    float cum_g = acc + __shfl_sync(0xffffffffu, cum, last);
+    float next_in = __shfl_sync(0xffffffffu, k, min(last + 1, 31));
+    if (lane == 0) {
+      float next = (last + 1 < m) ? next_in : s.above;
+      if (m > 0 && z < kInf) finalize(s, z, own, cum_g, next, cur);
+      else { s.flag = 1; s.zstar = cur; s.owner = kNone; }  // rounding left nothing: no move
+    }
+    __syncwarp();
+  }
+  gsync<G>();
+}
+
+// ------------------------------------------------------------------ warp-0 algebra
+
+// (warp 0) normal of constraint `cd` into v[0..p)
+__device__ __forceinline__ void normal_to(St& s, int cd, float* v) {
+  const int lane = threadIdx.x & 31;
+  for (int c = lane; c < s.p; c += 32)
+    v[c] = cd >= 0 ? s.Xq[(int64_t)c * s.ld + cd] : (c == -cd - 1 ? 1.f : 0.f);
+}
+
+// (warp 0) try to add constraint cd to the echelon rows Bm[0..m)
+__device__ __noinline__ bool try_add(St& s, int cd, int m) {
+  const int lane = threadIdx.x & 31, p = s.p;
+  float* v = s.tv;
+  normal_to(s, cd, v);
+  __syncwarp();
+  float vmax0 = 0.f;
+  for (int c = lane; c < p; c += 32) vmax0 = fmaxf(vmax0, fabsf(v[c]));
+  vmax0 = warp_max(vmax0);
+  if (!(vmax0 > 0.f)) return false;
+  for (int q = 0; q < m; ++q) {
+    const float* e = s.Bm + q * p;
+    float f = v[s.pcol[q]] / e[s.pcol[q]];
+    __syncwarp();
+    if (f != 0.f)
+      for (int c = lane; c < p; c += 32) v[c] -= f * e[c];
+    __syncwarp();
+  }
+  float bvv = 0.f;
+  int bj = p;
+  for (int c = lane; c < p; c += 32)
+    if (fabsf(v[c]) > bvv) { bvv = fabsf(v[c]); bj = c; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float ov = __shfl_xor_sync(0xffffffffu, bvv, o);
+    int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+    if (ov > bvv || (ov == bvv && oj < bj)) { bvv = ov; bj = oj; }
+  }
+  if (!(bvv > 1e-4f * vmax0)) return false;
+  for (int c = lane; c < p; c += 32) s.Bm[m * p + c] = v[c];
+  if (lane == 0) s.pcol[m] = bj;
+  __syncwarp();
+  return true;
+}
+
+// (warp 0) basis at a CCD fixed point: the hyperplanes the axis steps landed
+// on (kept when independent), completed with coordinate hyperplanes.
+__device__ __noinline__ void build_basis(St& s) {
+  const int lane = threadIdx.x & 31, p = s.p;
+  int m = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j = 0; j < p && m < p; ++j) {
+      int cd;
+      if (pass == 0) {
+        int pv = s.piv[j];
+        if (pv == -2) continue;
+        cd = pv >= 0 ? pv : coord_code(j);
+      } else {
+        cd = coord_code(j);
+      }
+      bool dup = false;
+      for (int q = 0; q < m; ++q) dup |= s.code[q] == cd;
+      if (dup) continue;
+      if (try_add(s, cd, m)) {
+        if (lane == 0) { s.code[m] = cd; s.phan[m] = pass == 1 && s.bv[j] != 0.f; }
+        __syncwarp();
+        ++m;
+      }
+    }
+  }
+  for (int j = 0; m < p && j < p; ++j) {  // unreachable: coordinates span
+    if (lane == 0) { s.code[m] = coord_code(j); s.phan[m] = s.bv[j] != 0.f; }
+    __syncwarp();
+    ++m;
+  }
+}
+
+// (warp 0) LU with partial pivoting of Bm in place; perm[k] = original row.
+__device__ __noinline__ bool lu(St& s) {
+  const int lane = threadIdx.x & 31, p = s.p;
+  float* B = s.Bm;
+  for (int c = lane; c < p; c += 32) s.perm[c] = c;
+  float amax = 0.f;
+  for (int e = lane; e < p * p; e += 32) amax = fmaxf(amax, fabsf(B[e]));
+  amax = warp_max(amax);
+  __syncwarp();
+  for (int k = 0; k < p; ++k) {
+    float bvv = -1.f;
+    int bi = k;
+    for (int i = k + lane; i < p; i += 32)
+      if (fabsf(B[i * p + k]) > bvv) { bvv = fabsf(B[i * p + k]); bi = i; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float ov = __shfl_xor_sync(0xffffffffu, bvv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bvv || (ov == bvv && oi < bi)) { bvv = ov; bi = oi; }
+    }
+    if (!(bvv > 1e-7f * amax)) return false;
+    if (bi != k) {
+      for (int c = lane; c < p; c += 32) {
+        float t = B[k * p + c]; B[k * p + c] = B[bi * p + c]; B[bi * p + c] = t;
+      }
+      if (lane == 0) { int t = s.perm[k]; s.perm[k] = s.perm[bi]; s.perm[bi] = t; }
+    }
+    __syncwarp();
+    float pv = B[k * p + k];
+    for (int i = k + 1 + lane; i < p; i += 32) B[i * p + k] /= pv;
+    __syncwarp();
+    int rem = p - k - 1;
+    for (int e = lane; e < rem * rem; e += 32) {
+      int i = k + 1 + e / rem, c = k + 1 + e % rem;
+      B[i * p + c] -= B[i * p + k] * B[k * p + c];
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
+// (warp 0) solve B x = rhs, rhs in x (overwritten), with the LU in Bm.
+__device__ __noinline__ void lu_solve(St& s, float* x) {
+  const int lane = threadIdx.x & 31, p = s.p;
+  const float* B = s.Bm;
+  float* t = s.tv;
+  for (int c = lane; c < p; c += 32) t[c] = x[s.perm[c]];
+  __syncwarp();
+  for (int k = 0; k < p; ++k) {
+    float v = t[k];
+    for (int i = k + 1 + lane; i < p; i += 32) t[i] -= B[i * p + k] * v;
+    __syncwarp();
+  }
+  for (int k = p - 1; k >= 0; --k) {
+    if (lane == 0) t[k] /= B[k * p + k];
+    __syncwarp();
+    float v = t[k];
+    for (int i = lane; i < k; i += 32) t[i] -= B[i * p + k] * v;
+    __syncwarp();
+  }
+  for (int c = lane; c < p; c += 32) x[c] = t[c];
+  __syncwarp();
+}
+
+// (warp 0) solve B^T x = rhs with the LU (B = P^T L U).
+__device__ __noinline__ void lu_solve_t(St& s, float* x) {
+  const int lane = threadIdx.x & 31, p = s.p;
+  const float* B = s.Bm;
+  float* t = s.tv;
+  for (int c = lane; c < p; c += 32) t[c] = x[c];
+  __syncwarp();
+  for (int k = 0; k < p; ++k) {
+    if (lane == 0) t[k] /= B[k * p + k];
+    __syncwarp();
+    float v = t[k];
+    for (int i = k + 1 + lane; i < p; i += 32) t[i] -= B[k * p + i] * v;
+    __syncwarp();
+  }
+  for (int k = p - 1; k >= 0; --k) {
+    float v = t[k];
+    for (int i = lane; i < k; i += 32) t[i] -= B[k * p + i] * v;
+    __syncwarp();
+  }
+  for (int c = lane; c < p; c += 32) x[s.perm[c]] = t[c];
+  __syncwarp();
+}
+
+// (warp 0) form the basis matrix, factor it and snap b onto the basis
+// hyperplanes (phantom coordinates keep their value).  Sets s.flag.
+__device__ __noinline__ void snap(St& s) {
+  const int lane = threadIdx.x & 31, p = s.p;
+  for (int k = 0; k < p; ++k) normal_to(s, s.code[k], s.Bm + k * p);
+  for (int k = lane; k < p; k += 32) {
+    int cd = s.code[k];
+    s.hv[k] = cd >= 0 ? s.yq[cd] : (s.phan[k] ? s.bv[-cd - 1] : 0.f);
+  }
+  __syncwarp();
+  bool ok = lu(s);
+  if (lane == 0) s.flag = ok;
+  if (ok) {
+    lu_solve(s, s.hv);
+    for (int c = lane; c < p; c += 32) s.bv[c] = s.hv[c];
+    __syncwarp();
+    for (int k = lane; k < p; k += 32)
+      if (s.code[k] < 0 && !s.phan[k]) s.bv[-s.code[k] - 1] = 0.f;
+  }
+  __syncwarp();
+}
+
+// (warp 0) multipliers from the column sums in red2, pick the most violated
+// basis hyperplane, and (if stepping) the edge direction dv.
+template <int G>
+__device__ __noinline__ void multipliers(St& s, bool step) {
+  constexpr int W = G / 32;
+  const int lane = threadIdx.x & 31, p = s.p;
+  const float lam = s.lam;
+  for (int c = lane; c < p; c += 32) {
+    float g = 0.f;
+    for (int w = 0; w < W; ++w) g += s.red2[w * p + c];
+    bool real = false;
+    for (int k = 0; k < p; ++k) real |= (s.code[k] == coord_code(c) && !s.phan[k]);
+    if (!real) g += lam * fsign(s.bv[c]);
+    s.mu[c] = -g;
+  }
+  __syncwarp();
+  lu_solve_t(s, s.mu);
+  const float tol = s.a->o.tol_opt * fmaxf(1.f, lam);
+  float worst = tol;
+  int q = -1, phantoms = 0, atcap = 0;
+  for (int k = lane; k < p; k += 32) {
+    float cap = s.code[k] >= 0 ? 1.f : (s.phan[k] ? 0.f : lam);
+    float viol = fabsf(s.mu[k]) - cap;
+    if (s.phan[k]) phantoms++;
+    else if (viol > -1e-4f * fmaxf(1.f, cap)) atcap++;
+    if (viol > worst) { worst = viol; q = k; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float ov = __shfl_xor_sync(0xffffffffu, worst, o);
+    int oq = __shfl_xor_sync(0xffffffffu, q, o);
+    if (ov > worst || (ov == worst && oq >= 0 && (q < 0 || oq < q))) { worst = ov; q = oq; }
+  }
+  phantoms = warp_sum_i(phantoms);
+  atcap = warp_sum_i(atcap);
+  if (lane == 0) { s.q = q; s.iter = (phantoms > 0 || atcap > 0); }
+  __syncwarp();
+  if (q >= 0 && step) {
+    float sg = s.mu[q] > 0.f ? 1.f : -1.f;
+    for (int c = lane; c < p; c += 32) s.dv[c] = c == q ? sg : 0.f;
+    __syncwarp();
+    lu_solve(s, s.dv);
+  }
+}
+
+// (thread 0) coordinate breakpoints of the edge line search, appended to the
+// selection buffer after the n rows.  Returns their count.
+__device__ __noinline__ int edge_specials(St& s, int q) {
+  const int p = s.p, n = s.n;
+  int ns = 0;
+  for (int c = 0; c < p; ++c) {
+    int kk = -1;
+    for (int k = 0; k < p; ++k) if (s.code[k] == coord_code(c)) kk = k;
+    if (kk >= 0 && kk != q) continue;  // other basis coordinates stay at 0
+    float dc = s.dv[c];
+    if (kk == q && !s.phan[q]) {
+      s.ck[n + ns] = 0.f; s.cw[n + ns] = s.lam * fabsf(dc); s.cid[n + ns] = coord_code(c); ++ns;
+    } else if (dc != 0.f) {
+      s.ck[n + ns] = -s.bv[c] / dc; s.cw[n + ns] = s.lam * fabsf(dc); s.cid[n + ns] = coord_code(c); ++ns;
+    }
+  }
+  return ns;
+}
+
+// ------------------------------------------------------------------ row passes
+// The residual lives in shared memory (s.rr); threads stride over rows.
+
+template <int G>
+__device__ __forceinline__ void recompute_r(St& s) {
+  const int n = s.n, p = s.p, ld = s.ld;
+  for (int i = threadIdx.x; i < n; i += G) {
+    float v = s.yq[i];
+    for (int c = 0; c < p; ++c) v -= s.Xq[(int64_t)c * ld + i] * s.bv[c];
+    s.rr[i] = v;
+  }
+}
+
+template <int G>
+__device__ __forceinline__ float objective(St& s) {
+  float a = 0.f;
+  for (int i = threadIdx.x; i < s.n; i += G) a += fabsf(s.rr[i]);
+  float b = 0.f;
+  if (threadIdx.x < 32)
+    for (int c = threadIdx.x; c < s.p; c += 32) b += fabsf(s.bv[c]);
+  float bs;
+  float as = gsum2<G>(s, a, b, bs);
+  return as + s.lam * bs;
+}
+
+// Exact minimisation along axis j (Section 3.3): the weighted median of
+// z_i = b_j + r_i / x_ij (weights |x_ij|) and 0 (weight lambda).  Returns
+// the move; records the breakpoint landed on in piv[j].
+template <int G>
+__device__ __noinline__ float axis_update(St& s, int j) {
+  const int n = s.n;
+  const float* col = s.Xq + (int64_t)j * s.ld;
+  const float bj = s.bv[j];
+  for (int i = threadIdx.x; i < n; i += G) {
+    float x = col[i];
+    s.ck[i] = x != 0.f ? bj + __fdividef(s.rr[i], x) : kInf;
+    s.cw[i] = fabsf(x);
+  }
+  const int ns = s.lam > 0.f ? 1 : 0;
+  if (threadIdx.x == 0 && ns) { s.ck[n] = 0.f; s.cw[n] = s.lam; s.cid[n] = coord_code(j); }
+  gsync<G>();
+  select<G>(s, n + ns, bj);
+  const float z = s.zstar;
+  const int own = s.owner;
+  const float d = z - bj;
+  if (d != 0.f)
+    for (int i = threadIdx.x; i < n; i += G) s.rr[i] -= col[i] * d;
+  gsync<G>();
+  if (threadIdx.x == 0) {
+    s.bv[j] = z;
+    s.piv[j] = own == kNone ? -2 : (own < 0 ? -1 : own);
+  }
+  gsync<G>();
+  return d;
+}
+
+// Cyclical coordinate descent (Section 3.3) skipping axis `skip`.
+template <int G>
+__device__ __noinline__ int ccd(St& s, int skip, int max_sweeps) {
+  const float tol = s.a->o.tol_move;
+  for (int sw = 1; sw <= max_sweeps; ++sw) {
+    float mx = 0.f;
+    for (int j = 0; j < s.p; ++j) {
+      if (j == skip) continue;
+      mx = fmaxf(mx, fabsf(axis_update<G>(s, j)));
+    }
+    float bmax = 0.f;
+    for (int c = 0; c < s.p; ++c) bmax = fmaxf(bmax, fabsf(s.bv[c]));
+    if (mx <= tol * fmaxf(1.f, bmax)) return sw;
+  }
+  return -max_sweeps;
+}
+
+// One chop probe: b_k := t, restricted CCD from the previous probe's point.
+template <int G>
+__device__ __forceinline__ float probe(St& s, int k, float t, float& best_f, int& sweeps,
+                                       int& probes) {
+  const float d = t - s.bv[k];
+  if (d != 0.f) {
+    const float* col = s.Xq + (int64_t)k * s.ld;
+    for (int i = threadIdx.x; i < s.n; i += G) s.rr[i] -= col[i] * d;
+  }
+  gsync<G>();
+  if (threadIdx.x == 0) s.bv[k] = t;
+  gsync<G>();
+  int sw = ccd<G>(s, k, s.a->o.probe_max_sweeps);
+  sweeps += sw < 0 ? -sw : sw;
+  probes += 1;
+  float f = objective<G>(s);
+  if (f < best_f) {
+    best_f = f;
+    for (int c = threadIdx.x; c < s.p; c += G) s.bbest[c] = s.bv[c];
+  }
+  gsync<G>();
+  return f;
+}
+
+// Ternary chop on axis k (Sections 3.4-3.5): bracket around b_k, move the
+// bracket while an end is lower than the centre (range extension), then
+// ternary steps; b ends at the best probe (or the start if none improved).
+template <int G>
+__device__ __noinline__ void chop(St& s, int k, int& sweeps, int& probes) {
+  const Opts& o = s.a->o;
+  const float f0 = objective<G>(s);
+  float best_f = f0;
+  for (int c = threadIdx.x; c < s.p; c += G) s.bbest[c] = s.bv[c];
+  gsync<G>();
+  const float c0 = s.bv[k];
+  const float scale = fmaxf(1.f, fabsf(c0));
+  float delta = o.chop_bracket * scale;
+  float pa = c0 - delta, pm = c0, pe = c0 + delta, gm = f0;
+  float ga = probe<G>(s, k, pa, best_f, sweeps, probes);
+  float ge = probe<G>(s, k, pe, best_f, sweeps, probes);
+  for (int ext = 0; ext < o.chop_max_extend; ++ext) {
+    if (ga < gm) {
+      pe = pm; ge = gm; pm = pa; gm = ga; delta *= 2.f; pa = pm - delta;
+      ga = probe<G>(s, k, pa, best_f, sweeps, probes);
+    } else if (ge < gm) {
+      pa = pm; ga = gm; pm = pe; gm = ge; delta *= 2.f; pe = pm + delta;
+      ge = probe<G>(s, k, pe, best_f, sweeps, probes);
+    } else {
+      break;
+    }
+  }
+  float lo = pa, hi = pe;
+  int np = 0;
+  while (hi - lo > o.chop_tol * scale && np + 2 <= o.chop_max_probes) {
+    float m1 = lo + (hi - lo) / 3.f, m2 = hi - (hi - lo) / 3.f;
+    float g1 = probe<G>(s, k, m1, best_f, sweeps, probes);
+    float g2 = probe<G>(s, k, m2, best_f, sweeps, probes);
+    np += 2;
+    if (g1 < g2) hi = m2;
+    else if (g1 > g2) lo = m1;
+    else { lo = m1; hi = m2; }
+  }
+  for (int c = threadIdx.x; c < s.p; c += G) s.bv[c] = s.bbest[c];
+  gsync<G>();
+  recompute_r<G>(s);
+  gsync<G>();
+}
+
+// Exact polish from the current basis (code/phan); max_piv = 0 only tests.
+template <int G>
+__device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonunique) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = s.n, p = s.p, ld = s.ld;
+  int it = 0;
+  *is_opt = 0;
+  *nonunique = 0;
+  for (;;) {
+    if (warp == 0) snap(s);
+    gsync<G>();
+    if (!s.flag) break;  // singular basis: give up (status MAX_ITERS)
+    recompute_r<G>(s);
+    for (int w = tid; w < s.maskw; w += G) s.mask[w] = 0u;
+    gsync<G>();
+    if (tid == 0)
+      for (int k = 0; k < p; ++k)
+        if (s.code[k] >= 0) s.mask[s.code[k] >> 5] |= 1u << (s.code[k] & 31);
+    gsync<G>();
+    // column sums g_c = -sum_{rows not in basis} sign(r_i) x_ic
+    for (int c = 0; c < p; ++c) {
+      const float* col = s.Xq + (int64_t)c * ld;
+      float a = 0.f;
+      for (int i = tid; i < n; i += G)
+        if (!((s.mask[i >> 5] >> (i & 31)) & 1u)) a -= fsign(s.rr[i]) * col[i];
+      a = warp_sum(a);
+      if (lane == 0) s.red2[warp * p + c] = a;
+    }
+    gsync<G>();
+    if (warp == 0) multipliers<G>(s, it < max_piv);
+    gsync<G>();
+    const int q = s.q;
+    if (q < 0) { *is_opt = 1; *nonunique = s.iter; break; }
+    if (it >= max_piv) break;
+    // edge line search: breakpoints of t -> F(b + t d)
+    const int qcode = s.code[q];
+    for (int i = tid; i < n; i += G) {
+      float v = 0.f;
+      for (int c = 0; c < p; ++c) v += s.Xq[(int64_t)c * ld + i] * s.dv[c];
+      bool inb = (s.mask[i >> 5] >> (i & 31)) & 1u;
+      if (inb && i != qcode) v = 0.f;  // other basis rows stay on their hyperplanes
+      s.ck[i] = i == qcode ? 0.f : (v != 0.f ? __fdividef(s.rr[i], v) : kInf);
+      s.cw[i] = fabsf(v);
+    }
+    if (tid == 0) s.m = edge_specials(s, q);
+    gsync<G>();
+    const int ns = s.m;
+    gsync<G>();
+    select<G>(s, n + ns, 0.f);
+    const float ts = s.zstar;
+    const int own = s.owner;
+    if (own == kNone) break;  // flat along the edge (cannot happen when F decreases)
+    if (warp == 0) {
+      for (int c = lane; c < p; c += 32) s.bv[c] += ts * s.dv[c];
+      __syncwarp();
+      if (lane == 0) { s.code[q] = own; s.phan[q] = 0; }
+    }
+    gsync<G>();
+    ++it;
+  }
+  gsync<G>();
+  return it;
+}
+
+// ------------------------------------------------------------------ one problem
+
+template <int G>
+__device__ __forceinline__ void write_bad_path(St& s, int q) {
+  const FitArgs& A = *s.a;
+  for (int l = 0; l < A.L; ++l) {
+    int64_t f = (int64_t)q * A.L + l;
+    for (int c = threadIdx.x; c < A.P; c += G) {
+      A.b_out[f * A.P + c] = 0.f;
+      if (A.basis_out) A.basis_out[f * A.P + c] = coord_code(c);
+    }
+    if (threadIdx.x == 0) {
+      A.obj_out[f] = 0.f;
+      if (A.status) A.status[f] = kFitBadInput;
+      if (A.counters) for (int e = 0; e < 4; ++e) A.counters[f * 4 + e] = 0;
+    }
+  }
+}
+
+template <int G>
+__device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
+  const int tid = threadIdx.x;
+  const FitArgs& A = *s.a;
+  int64_t o0 = 0;
+  int n = 0, p = 0;
+  bool ok = problem_ok(A, q, o0, n, p, ncap);
+  int bad = 0;
+  float* Xw = nullptr;
+  int ld = 0;
+  if (ok) {
+    ld = (int)xg_ld(n);
+    Xw = A.Xg + xg_base(o0, q, A.P4);
+    for (int64_t e = tid; e < (int64_t)n * p; e += G) {
+      int c = (int)(e / n), i = (int)(e % n);
+      int64_t row = A.row_idx ? (int64_t)A.row_idx[o0 + i] : o0 + i;
+      if (row < 0 || row >= A.rows_X) { bad = 1; continue; }
+      float v = A.X[row * A.ldX + c];
+      if (!isfinite(v)) bad = 1;
+      Xw[(int64_t)c * ld + i] = v;
+    }
+    for (int i = tid; i < n; i += G) if (!isfinite(A.y[o0 + i])) bad = 1;
+  }
+  {
+    float f[1] = {0.f}, m[1] = {kInf};
+    int si[1] = {bad}, mi[1] = {0};
+    reduce<G, 1, 1, 1, 1>(s, f, m, si, mi);
+    ok = ok && si[0] == 0;
+  }
+  __syncthreads();
+  if (!ok) { write_bad_path<G>(s, q); return; }
+  if (tid == 0) {
+    s.n = n; s.p = p; s.ld = ld;
+    s.Xq = Xw; s.yq = A.y + o0;
+  }
+  __syncthreads();
+  for (int c = tid; c < p; c += G) s.bv[c] = A.b_init ? A.b_init[(int64_t)q * A.P + c] : 0.f;
+  __syncthreads();
+  recompute_r<G>(s);
+  __syncthreads();
+  for (int l = 0; l < A.L; ++l) {
+    const int64_t f = (int64_t)q * A.L + l;
+    const float lraw = A.lambdas[f];
+    if (!(lraw >= 0.f) || !isfinite(lraw)) {
+      for (int c = tid; c < A.P; c += G) {
+        A.b_out[f * A.P + c] = 0.f;
+        if (A.basis_out) A.basis_out[f * A.P + c] = coord_code(c);
+      }
+      if (tid == 0) {
+        A.obj_out[f] = 0.f;
+        if (A.status) A.status[f] = kFitBadInput;
+        if (A.counters) for (int e = 0; e < 4; ++e) A.counters[f * 4 + e] = 0;
+      }
+      continue;
+    }
+    if (tid == 0) s.lam = fmaxf(lraw, A.o.lambda_min_floor);
+    for (int c = tid; c < p; c += G) s.piv[c] = -2;
+    __syncthreads();
+    int status = kFitOk, sweeps = 0, probes = 0, pivots = 0, flags = 0;
+    int sw = ccd<G>(s, -1, A.o.max_sweeps);
+    sweeps += sw < 0 ? -sw : sw;
+    if (sw < 0) status |= kFitMaxIters;
+    int is_opt = 0, nonu = 0;
+    if (tid < 32) build_basis(s);
+    __syncthreads();
+    polish<G>(s, 0, &is_opt, &nonu);
+    if (is_opt) flags |= 1;
+    if (!is_opt && A.o.chop && p >= 2) {
+      // Section 3.4: any axis will do; take the largest |b_k|
+      int kax = 0;
+      for (int c = 1; c < p; ++c) if (fabsf(s.bv[c]) > fabsf(s.bv[kax])) kax = c;
+      __syncthreads();
+      flags |= 2;
+      chop<G>(s, kax, sweeps, probes);
+      for (int c = tid; c < p; c += G) s.piv[c] = -2;
+      __syncthreads();
+      sw = ccd<G>(s, -1, A.o.max_sweeps);
+      sweeps += sw < 0 ? -sw : sw;
+      if (tid < 32) build_basis(s);
+      __syncthreads();
+      polish<G>(s, 0, &is_opt, &nonu);
+      if (is_opt) flags |= 4;
+    }
+    if (!is_opt && A.o.polish) {
+      if (tid < 32) build_basis(s);
+      __syncthreads();
+      const int mp = A.o.max_pivots > 0 ? A.o.max_pivots : 4 * p + 64;
+      pivots = polish<G>(s, mp, &is_opt, &nonu);
+      if (!is_opt) status |= kFitMaxIters;
+    }
+    if (is_opt && nonu) status |= kFitNonunique;
+    const float F = objective<G>(s);
+    for (int c = tid; c < A.P; c += G) {
+      A.b_out[f * A.P + c] = c < p ? s.bv[c] : 0.f;
+      if (A.basis_out) A.basis_out[f * A.P + c] = c < p ? s.code[c] : coord_code(c);
+    }
+    if (tid == 0) {
+      A.obj_out[f] = F;
+      if (A.status) A.status[f] = status;
+      if (A.counters) {
+        A.counters[f * 4 + 0] = sweeps;
+        A.counters[f * 4 + 1] = probes;
+        A.counters[f * 4 + 2] = pivots;
+        A.counters[f * 4 + 3] = flags;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Shared-memory bytes for a block of G threads, row capacity ncap, P columns.
+template <int G>
+size_t smem_bytes(int ncap, int P) {
+  constexpr int W = G / 32;
+  size_t cap = (size_t)ncap + P + 1;
+  size_t words = 4 * cap + 6 * (size_t)P + (size_t)P * P + (size_t)W * P + 5 * (size_t)P +
+                 (size_t)ncap / 32 + 1 + 2 * (size_t)W * 16 + 64;
+  return words * 4 + 16;
+}
+
+template <int G>
+__device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
+  constexpr int W = G / 32;
+  s.cap = ncap + P + 1;
+  s.maskw = ncap / 32 + 1;
+  float* f = reinterpret_cast<float*>(raw);
+  s.rr = f; f += s.cap;
+  s.ck = f; f += s.cap;
+  s.cw = f; f += s.cap;
+  s.cid = reinterpret_cast<int*>(f); f += s.cap;
+  s.bv = f; f += P; s.bbest = f; f += P; s.dv = f; f += P;
+  s.mu = f; f += P; s.tv = f; f += P; s.hv = f; f += P;
+  s.Bm = f; f += P * P;
+  s.red2 = f; f += W * P;
+  int* ip = reinterpret_cast<int*>(f);
+  s.code = ip; ip += P; s.phan = ip; ip += P; s.piv = ip; ip += P; s.perm = ip; ip += P;
+  s.pcol = ip; ip += P;
+  f = reinterpret_cast<float*>(ip);
+  s.mask = reinterpret_cast<unsigned*>(f); f += s.maskw;
+  s.redf = f; f += W * 16;
+  s.redi = reinterpret_cast<int*>(f); f += W * 16;
+  s.sampk = f; f += 32;
+  s.sampw = f; f += 32;
+}
+
+template <int G>
+__global__ void __launch_bounds__(G) fit_block_kernel(FitArgs args, int ncap) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ St s;
+  __shared__ FitArgs A;
+  if (threadIdx.x == 0) {
+    A = args;
+    carve<G>(s, smem_raw, ncap, args.P);
+    s.a = &A;
+  }
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) s.q = atomicAdd(A.queue, 1);
+    __syncthreads();
+    const int q = s.q;
+    __syncthreads();
+    if (q >= A.B) break;
+    run_problem<G>(s, q, ncap);
+    __syncthreads();
+  }
+}
+
+template <int G>
+cudaError_t launch_variant(const FitArgs& a, cudaStream_t st, int num_sms, int ncap) {
+  size_t smem = smem_bytes<G>(ncap, a.P);
+  auto kern = fit_block_kernel<G>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int grid = per_sm * num_sms;
+  if (grid > a.B) grid = a.B;
+  if (grid < 1) grid = 1;
+  kern<<<grid, G, smem, st>>>(a, ncap);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Largest row capacity a block of G threads can hold with P columns in the
+// shared memory one block may use (227 KB).
+int fit_block_max_rows(int G, int P) {
+  const size_t limit = 227 * 1024;
+  int lo = 0, hi = 1 << 16;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) / 2;
+    size_t b = G == 32 ? smem_bytes<32>(mid, P) : G == 64 ? smem_bytes<64>(mid, P)
+             : G == 128 ? smem_bytes<128>(mid, P) : smem_bytes<256>(mid, P);
+    if (b <= limit) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Default block size for a problem set: more threads for longer problems.
+int fit_block_group(int n_max) {
+  if (n_max <= 256) return 32;
+  if (n_max <= 1024) return 64;
+  return 128;
+}
+
+cudaError_t launch_fit_block(const FitArgs& a, cudaStream_t st, int num_sms, int G) {
+  int ncap = (a.n_max + 31) & ~31;
+  if (ncap < 32) ncap = 32;
+  switch (G) {
+    case 32: return launch_variant<32>(a, st, num_sms, ncap);
+    case 64: return launch_variant<64>(a, st, num_sms, ncap);
+    case 128: return launch_variant<128>(a, st, num_sms, ncap);
+    case 256: return launch_variant<256>(a, st, num_sms, ncap);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ll

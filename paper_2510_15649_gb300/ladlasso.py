@@ -1,0 +1,231 @@
+"""ctypes binding of libladlasso.so (argument marshalling only).
+
+Every step of the fit runs in the CUDA library; this module only turns torch
+device tensors into pointers and sizes, allocates outputs and the workspace
+with torch, and passes the current CUDA stream.  There is no CPU path: if the
+library is not built, `lib()` raises.
+
+Names follow include/ladlasso.h.  The batch layout ("problem set") is the
+one documented there: X [rows_X, ldX] float32 row-major, y [total_rows],
+row_idx [total_rows] int32 or None, offsets [B+1] int64, p [B] int32 or None.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libladlasso.so")
+_lib = None
+
+OK, ERR_INVALID, ERR_CUDA, ERR_NOMEM, ERR_WORKSPACE = 0, -1, -2, -3, -4
+FIT_OK, FIT_MAX_ITERS, FIT_BAD_INPUT, FIT_NONUNIQUE = 0, 1, 2, 4
+
+
+class Opts(C.Structure):
+    _fields_ = [("tol_move", C.c_float), ("max_sweeps", C.c_int32), ("chop", C.c_int32),
+                ("chop_bracket", C.c_float), ("chop_tol", C.c_float),
+                ("chop_max_probes", C.c_int32), ("chop_max_extend", C.c_int32),
+                ("probe_max_sweeps", C.c_int32), ("polish", C.c_int32),
+                ("max_pivots", C.c_int32), ("tol_opt", C.c_float),
+                ("lambda_min_floor", C.c_float)]
+
+
+class Dims(C.Structure):
+    _fields_ = [("B", C.c_int32), ("P_cols", C.c_int32), ("L", C.c_int32), ("n_max", C.c_int32),
+                ("ldX", C.c_int64), ("rows_X", C.c_int64), ("total_rows", C.c_int64),
+                ("p", C.c_void_p), ("b_init", C.c_void_p), ("fit_status", C.c_void_p),
+                ("basis_out", C.c_void_p), ("counters", C.c_void_p), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_size_t), ("opts", C.c_void_p)]
+
+
+class LadLassoError(RuntimeError):
+    pass
+
+
+SYMBOLS = ["ladlasso_default_opts", "ladlasso_workspace_size", "ladlasso_lambda_max",
+           "ladlasso_lambda_path", "ladlasso_fit_batched", "ladlasso_fit_batched_thread",
+           "ladlasso_fit_backward", "ladlasso_status_string"]
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise LadLassoError(f"{LIB_PATH} is not built; run paper_2510_15649_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    P, I32, I64, F = C.c_void_p, C.c_int32, C.c_int64, C.c_float
+    DP = C.POINTER(Dims)
+    L.ladlasso_default_opts.argtypes = [C.POINTER(Opts)]
+    L.ladlasso_default_opts.restype = None
+    L.ladlasso_workspace_size.argtypes = [I32, I32, I64, I32]
+    L.ladlasso_workspace_size.restype = C.c_size_t
+    L.ladlasso_lambda_max.argtypes = [P, P, P, P, DP, P, P]
+    L.ladlasso_lambda_max.restype = C.c_int
+    L.ladlasso_lambda_path.argtypes = [P, I32, I32, F, P, P]
+    L.ladlasso_lambda_path.restype = C.c_int
+    for nm in ("ladlasso_fit_batched", "ladlasso_fit_batched_thread"):
+        fn = getattr(L, nm)
+        fn.argtypes = [P, P, P, P, P, P, P, DP, P]
+        fn.restype = C.c_int
+    L.ladlasso_fit_backward.argtypes = [P, P, P, P, DP, I32, P, P, P, I64, P, P, P, I64, P,
+                                        P, P, P, P, P, P, P]
+    L.ladlasso_fit_backward.restype = C.c_int
+    L.ladlasso_status_string.argtypes = [C.c_int]
+    L.ladlasso_status_string.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise LadLassoError(f"ladlasso: {lib().ladlasso_status_string(rc).decode()} ({rc})")
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().ladlasso_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class Problems:
+    """A problem set resident on the device (see include/ladlasso.h)."""
+    X: torch.Tensor
+    y: torch.Tensor
+    offsets: torch.Tensor
+    row_idx: torch.Tensor | None = None
+    p: torch.Tensor | None = None
+    P: int = 0
+    n_max: int = 0
+
+    @staticmethod
+    def from_numpy(batch: dict, device="cuda") -> "Problems":
+        """Upload a batch dict (synth layout) to `device`."""
+        import numpy as np
+        X = torch.as_tensor(np.ascontiguousarray(batch["X"], np.float32), device=device)
+        y = torch.as_tensor(np.ascontiguousarray(batch["y"], np.float32), device=device)
+        off = np.asarray(batch["offsets"], np.int64)
+        offsets = torch.as_tensor(off, device=device)
+        ri = batch.get("row_idx")
+        row_idx = None if ri is None else torch.as_tensor(np.ascontiguousarray(ri, np.int32), device=device)
+        p = torch.as_tensor(np.asarray(batch["p"], np.int32), device=device)
+        n_max = int(np.max(np.diff(off))) if len(off) > 1 else 0
+        return Problems(X=X, y=y, offsets=offsets, row_idx=row_idx, p=p,
+                        P=int(X.shape[1]), n_max=n_max)
+
+    @property
+    def B(self) -> int:
+        return int(self.offsets.numel()) - 1
+
+    def dims(self, L: int, workspace: torch.Tensor, opts: Opts | None = None, b_init=None,
+             status=None, basis=None, counters=None) -> Dims:
+        d = Dims()
+        d.B, d.P_cols, d.L, d.n_max = self.B, self.P, L, self.n_max
+        d.ldX = int(self.X.stride(0))
+        d.rows_X = int(self.X.shape[0])
+        d.total_rows = int(self.y.numel())
+        d.p = None if self.p is None else self.p.data_ptr()
+        d.b_init = None if b_init is None else b_init.data_ptr()
+        d.fit_status = None if status is None else status.data_ptr()
+        d.basis_out = None if basis is None else basis.data_ptr()
+        d.counters = None if counters is None else counters.data_ptr()
+        d.workspace = workspace.data_ptr()
+        d.workspace_bytes = workspace.numel()
+        d.opts = None if opts is None else C.addressof(opts)
+        return d
+
+
+def workspace_bytes(pr: Problems, L: int = 1) -> int:
+    n = lib().ladlasso_workspace_size(pr.B, pr.P, int(pr.y.numel()), L)
+    if n == 0:
+        raise LadLassoError("invalid sizes for workspace")
+    return int(n)
+
+
+def workspace(pr: Problems, L: int = 1) -> torch.Tensor:
+    """Workspace buffer for `pr` (torch allocation, 256-byte aligned)."""
+    n = workspace_bytes(pr, L)
+    return torch.empty(n, dtype=torch.uint8, device=pr.X.device)
+
+
+def lambda_max(pr: Problems, ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    ws = workspace(pr) if ws is None else ws
+    out = torch.empty(pr.B, dtype=torch.float32, device=pr.X.device)
+    d = pr.dims(1, ws)
+    _check(lib().ladlasso_lambda_max(_ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets),
+                                     C.byref(d), _ptr(out), _stream(stream)))
+    return out
+
+
+def lambda_path(lmax: torch.Tensor, L: int, ratio: float = 1e-3, stream=None) -> torch.Tensor:
+    B = int(lmax.numel())
+    out = torch.empty((B, L), dtype=torch.float32, device=lmax.device)
+    _check(lib().ladlasso_lambda_path(_ptr(lmax), B, L, float(ratio), _ptr(out), _stream(stream)))
+    return out
+
+
+def fit(pr: Problems, lambdas: torch.Tensor, *, b_init=None, opts: Opts | None = None,
+        basis: bool = False, counters: bool = False, per_thread: bool = False,
+        ws: torch.Tensor | None = None, out: dict | None = None, stream=None) -> dict:
+    """Fit every problem along its lambda path.  lambdas: [B, L] float32 (device).
+    Returns dict(b [B,L,P], obj [B,L], status [B,L], basis?, counters?)."""
+    B, P = pr.B, pr.P
+    lam = lambdas.reshape(B, -1)
+    L = int(lam.shape[1])
+    dev = pr.X.device
+    ws = workspace(pr, L) if ws is None else ws
+    if out is None:
+        out = dict(b=torch.empty((B, L, P), dtype=torch.float32, device=dev),
+                   obj=torch.empty((B, L), dtype=torch.float32, device=dev),
+                   status=torch.empty((B, L), dtype=torch.int32, device=dev))
+        if basis:
+            out["basis"] = torch.empty((B, L, P), dtype=torch.int32, device=dev)
+        if counters:
+            out["counters"] = torch.empty((B, L, 4), dtype=torch.int32, device=dev)
+    d = pr.dims(L, ws, opts, b_init=b_init, status=out["status"], basis=out.get("basis"),
+                counters=out.get("counters"))
+    fn = lib().ladlasso_fit_batched_thread if per_thread else lib().ladlasso_fit_batched
+    _check(fn(_ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), _ptr(lam.contiguous()),
+              _ptr(out["b"]), _ptr(out["obj"]), C.byref(d), _stream(stream)))
+    return out
+
+
+def fit_backward(pr: Problems, fwd: dict, pos: int, val: Problems, grad_up: torch.Tensor,
+                 ws: torch.Tensor | None = None, opts: Opts | None = None, stream=None) -> dict:
+    """Gradient of sum_v |y_v - x_v b| per problem at path position `pos`
+    of a forward result that carries `basis`.  Returns dict(lam [B], y, X, yv, Xv, status)."""
+    B, P = pr.B, pr.P
+    L = int(fwd["b"].shape[1])
+    dev = pr.X.device
+    ws = workspace(pr, L) if ws is None else ws
+    g = dict(lam=torch.empty(B, dtype=torch.float32, device=dev),
+             y=torch.empty(pr.y.numel(), dtype=torch.float32, device=dev),
+             X=torch.empty((pr.y.numel(), P), dtype=torch.float32, device=dev),
+             yv=torch.empty(val.y.numel(), dtype=torch.float32, device=dev),
+             Xv=torch.empty((val.y.numel(), P), dtype=torch.float32, device=dev),
+             status=torch.empty(B, dtype=torch.int32, device=dev))
+    d = pr.dims(L, ws, opts)
+    _check(lib().ladlasso_fit_backward(
+        _ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), C.byref(d), int(pos),
+        _ptr(fwd["b"]), _ptr(fwd["basis"]), _ptr(val.X), int(val.X.stride(0)), _ptr(val.y),
+        _ptr(val.row_idx), _ptr(val.offsets), int(val.y.numel()), _ptr(grad_up.contiguous()),
+        _ptr(g["lam"]), _ptr(g["y"]), _ptr(g["X"]), _ptr(g["yv"]), _ptr(g["Xv"]),
+        _ptr(g["status"]), _stream(stream)))
+    return g

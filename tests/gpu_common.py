@@ -1,0 +1,53 @@
+"""Helpers shared by the GPU tests: run the CUDA path and compare with the
+FP64 oracle.  Parity bar (per fit, problem q at path position l):
+  rel. objective error |F(b_gpu) - F*| / F* <= 1e-5   (F evaluated in FP64)
+  same support {j : b_j != 0} when the oracle's optimum is unique
+  max_j |b_gpu - b*| <= 1e-4 * max(1, |b*|_inf)      when unique
+where F* and b* come from the oracle on the same float32 inputs and the
+same float32 lambdas, converted to float64."""
+import numpy as np
+
+import oracle
+
+REL_OBJ = 1e-5
+REL_COEF = 1e-4
+
+
+def compare(batch, lam, b_gpu, obj_gpu, status_gpu, problems=None, opts=None):
+    """Returns a dict of counts and the worst errors; asserts nothing."""
+    lam = np.asarray(lam, np.float64)
+    qs = range(lam.shape[0]) if problems is None else problems
+    worst_obj = 0.0
+    worst_coef = 0.0
+    bad = []
+    checked = 0
+    for q in qs:
+        X, y = oracle.problem(batch, q)
+        p = X.shape[1]
+        ref = oracle.fit_path(X, y, lam[q], opts=opts)
+        for l in range(lam.shape[1]):
+            checked += 1
+            if ref["status"][l] & oracle.FIT_BAD_INPUT:
+                if not (status_gpu[q, l] & 2):
+                    bad.append((q, l, "status"))
+                continue
+            bg = np.asarray(b_gpu[q, l, :p], np.float64)
+            fo = ref["f"][l]
+            fg = oracle.objective(X, y, bg, lam[q, l])
+            eo = abs(fg - fo) / max(1.0, fo)
+            worst_obj = max(worst_obj, eo)
+            if eo > REL_OBJ:
+                bad.append((q, l, "obj", eo))
+            if abs(obj_gpu[q, l] - fg) > 1e-5 * max(1.0, fg):
+                bad.append((q, l, "obj_out", obj_gpu[q, l], fg))
+            unique = not (ref["status"][l] & oracle.FIT_NONUNIQUE)
+            if unique:
+                if not np.array_equal(bg != 0, ref["b"][l] != 0):
+                    bad.append((q, l, "support"))
+                ec = np.max(np.abs(bg - ref["b"][l])) / max(1.0, np.max(np.abs(ref["b"][l])))
+                worst_coef = max(worst_coef, ec)
+                if ec > REL_COEF:
+                    bad.append((q, l, "coef", ec))
+            if np.any(b_gpu[q, l, p:] != 0):
+                bad.append((q, l, "padding"))
+    return dict(bad=bad, worst_obj=worst_obj, worst_coef=worst_coef, checked=checked)
