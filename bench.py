@@ -149,6 +149,10 @@ def row_updates(batch, counters, B):
     return float(np.sum((sw * p[:, None] + pv) * n[:, None]))
 
 
+def log(*a):
+    print("[bench]", *a, file=sys.stderr, flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -188,9 +192,11 @@ def main():
         return lam
 
     launches_per_step = 5  # 2 offset checks, lambda_max, lambda_path, fit
+    t0 = time.perf_counter()
     for _ in range(args.warmup):
         lam = step()
     torch.cuda.synchronize()
+    log(f"warmup {args.warmup} steps {time.perf_counter() - t0:.2f}s")
     times = []
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
@@ -206,6 +212,7 @@ def main():
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
     t_step = statistics.median(times)
+    log(f"timed steps {times}")
     if dist is not None:
         tt = torch.tensor([t_step], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -232,6 +239,7 @@ def main():
         torch.cuda.synchronize()
         kt.append(e0.elapsed_time(e1) / 1e3)
     t_fit = statistics.median(kt)
+    log(f"fit kernel {kt}")
 
     # end to end through the public API with pinned host buffers
     hX = torch.as_tensor(batch["X"]).pin_memory()
@@ -265,6 +273,7 @@ def main():
         torch.cuda.synchronize()
         et.append(e0.elapsed_time(e1) / 1e3)
     t_e2e = statistics.median(et)
+    log(f"e2e {et}")
 
     line = {"metric": METRIC, "value": value, "unit": "fits/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
@@ -316,7 +325,7 @@ def main():
     if not args.no_thread and rank == 0:
         try:
             tt = []
-            for _ in range(2):
+            for _ in range(1):
                 torch.cuda.synchronize()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -325,6 +334,7 @@ def main():
                 e1.record(stream)
                 torch.cuda.synchronize()
                 tt.append(e0.elapsed_time(e1) / 1e3)
+            log(f"thread-per-fit {tt}")
             s3 = o3["status"].cpu().numpy()
             line["thread_per_fit"] = {"fits_per_s": int(np.sum((s3 & 3) == 0)) / min(tt),
                                       "kernel_ms": 1e3 * min(tt)}

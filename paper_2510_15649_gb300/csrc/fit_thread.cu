@@ -4,8 +4,8 @@
 // CCD with exact weighted-median axis steps (Section 3.3), ternary chop with
 // restricted sub-searches and range extension (Sections 3.4-3.5), exact
 // vertex polish.  Each thread keeps its residual, selection buffer and basis
-// matrix in its own slice of the global workspace and reads its design rows
-// straight from X.
+// matrix in its own slice of the global workspace, and first copies its
+// design rows into its own column-major slice of the workspace.
 #include "common.cuh"
 
 namespace ll {
@@ -16,9 +16,10 @@ constexpr float kInf = INFINITY;
 struct TFit {
   // problem
   const FitArgs* a;
-  int q, n, p;
+  int q, n, p, ld;
   int64_t off0;
   float lam;
+  const float* Xq;   // gathered design, column c at Xq + c*ld
   // scratch (global)
   float* zk;   // [n + P + 1] keys
   float* zw;   // weights
@@ -28,10 +29,7 @@ struct TFit {
   float* bv; float* bbest; float* dv; float* mu; float* hv; float* tv;  // [P]
   int* code; int* phan; int* piv; int* perm; int* pcol;  // [P]
 
-  __device__ float x(int i, int c) const {
-    int64_t row = a->row_idx ? (int64_t)a->row_idx[off0 + i] : off0 + i;
-    return a->X[row * a->ldX + c];
-  }
+  __device__ __forceinline__ float x(int i, int c) const { return Xq[(int64_t)c * ld + i]; }
   __device__ float yv(int i) const { return a->y[off0 + i]; }
 
   // Weighted median of zk/zw/zi[0..m): smallest key whose cumulative weight
@@ -119,16 +117,22 @@ struct TFit {
   __device__ float axis_update(int j) {
     float bj = bv[j];
     int m = 0;
+    const float* __restrict__ col = Xq + (int64_t)j * ld;
+    const float* __restrict__ rr = r;
+    float* __restrict__ k_ = zk;
+    float* __restrict__ w_ = zw;
+    int* __restrict__ i_ = zi;
     for (int i = 0; i < n; ++i) {
-      float xv = x(i, j);
-      if (xv != 0.f) { zk[m] = bj + __fdividef(r[i], xv); zw[m] = fabsf(xv); zi[m] = i; ++m; }
+      float xv = col[i];
+      if (xv != 0.f) { k_[m] = bj + __fdividef(rr[i], xv); w_[m] = fabsf(xv); i_[m] = i; ++m; }
     }
     if (lam > 0.f) { zk[m] = 0.f; zw[m] = lam; zi[m] = coord_code(j); ++m; }
     int own;
     float z = wmedian(m, bj, &own);
     float d = z - bj;
     if (d != 0.f) {
-      for (int i = 0; i < n; ++i) r[i] -= x(i, j) * d;
+      float* __restrict__ rw = r;
+      for (int i = 0; i < n; ++i) rw[i] -= col[i] * d;
       bv[j] = z;
     }
     piv[j] = own == kNone ? -2 : (own < 0 ? -1 : own);
@@ -457,11 +461,20 @@ __global__ void __launch_bounds__(128) fit_thread_kernel(FitArgs args) {
   t.n = ok ? (int)(o1 - o0) : 0;
   t.p = p;
   if (ok) {
+    // validate and gather this problem's rows column-major into its own
+    // slice of the workspace
+    t.ld = (int)xg_ld(t.n);
+    float* Xw = args.Xg + xg_base(o0, q, args.P4);
     for (int i = 0; i < t.n && ok; ++i) {
       int64_t row = args.row_idx ? (int64_t)args.row_idx[o0 + i] : o0 + i;
       if (row < 0 || row >= args.rows_X || !isfinite(args.y[o0 + i])) { ok = false; break; }
-      for (int c = 0; c < p; ++c) if (!isfinite(args.X[row * args.ldX + c])) ok = false;
+      for (int c = 0; c < p; ++c) {
+        float v = args.X[row * args.ldX + c];
+        if (!isfinite(v)) ok = false;
+        Xw[(int64_t)c * t.ld + i] = v;
+      }
     }
+    t.Xq = Xw;
   }
   if (!ok) { t.write_bad(); return; }
   // scratch slices

@@ -4,13 +4,21 @@ FP64 oracle.  Parity bar (per fit, problem q at path position l):
   same support {j : b_j != 0} when the oracle's optimum is unique
   max_j |b_gpu - b*| <= 1e-4 * max(1, |b*|_inf)      when unique
 where F* and b* come from the oracle on the same float32 inputs and the
-same float32 lambdas, converted to float64."""
+same float32 lambdas, converted to float64.
+
+"Unique" means the oracle's certificate shows a strict vertex whose
+complementarity margin (1 - max|u_E|, 1 - max_off |X^T u|/lambda) is at
+least MARGIN.  Below that the optimum is degenerate to within float32
+resolution (e.g. lambda within rounding of lambda_max): several vertices
+reach F* to within 1e-5, so only the objective -- the one unique quantity --
+is compared there."""
 import numpy as np
 
 import oracle
 
 REL_OBJ = 1e-5
 REL_COEF = 1e-4
+MARGIN = 1e-4
 
 
 def compare(batch, lam, b_gpu, obj_gpu, status_gpu, problems=None, opts=None):
@@ -41,6 +49,10 @@ def compare(batch, lam, b_gpu, obj_gpu, status_gpu, problems=None, opts=None):
             if abs(obj_gpu[q, l] - fg) > 1e-5 * max(1.0, fg):
                 bad.append((q, l, "obj_out", obj_gpu[q, l], fg))
             unique = not (ref["status"][l] & oracle.FIT_NONUNIQUE)
+            if unique:
+                _, info = oracle.certify(X, y, ref["b"][l], lam[q, l])
+                margin = min(1.0 - info["u_e_max"], 1.0 - info["c_off_max"])
+                unique = info["unique"] and margin >= MARGIN
             if unique:
                 if not np.array_equal(bg != 0, ref["b"][l] != 0):
                     bad.append((q, l, "support"))

@@ -19,9 +19,11 @@ def ll():
     return ladlasso
 
 
-def _run(ll, batch, lam_np, per_thread=False, **kw):
+def _run(ll, batch, lam_np, per_thread=False, n_max=None, **kw):
     import torch
     pr = ll.Problems.from_numpy(batch)
+    if n_max is not None:
+        pr.n_max = n_max
     lam = torch.as_tensor(np.asarray(lam_np, np.float32), device="cuda")
     out = ll.fit(pr, lam, per_thread=per_thread, basis=True, counters=True, **kw)
     torch.cuda.synchronize()
@@ -90,13 +92,14 @@ def test_block_and_thread_kernels_agree(ll):
 def test_fit_is_identical_alone_and_in_a_batch(ll):
     batch = synth.batched_like(16, 30, 300, 2, 8, R=400, P=8, seed=5)
     lam = _oracle_lams(batch, 3, 1e-2)
+    n_max = int(np.max(np.diff(batch["offsets"])))
     full = _run(ll, batch, lam)
     for q in [0, 7, 15]:
         o0, o1 = batch["offsets"][q], batch["offsets"][q + 1]
         one = dict(X=batch["X"], y=batch["y"][o0:o1], row_idx=batch["row_idx"][o0:o1],
                    offsets=np.array([0, o1 - o0], np.int64), p=batch["p"][q:q + 1])
         # same n_max so the same block shape is used
-        alone = _run(ll, one, lam[q:q + 1])
+        alone = _run(ll, one, lam[q:q + 1], n_max=n_max)
         np.testing.assert_array_equal(alone["b"][0], full["b"][q])
         np.testing.assert_array_equal(alone["obj"][0], full["obj"][q])
 
