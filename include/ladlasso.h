@@ -187,6 +187,28 @@ int ladlasso_fit_backward(const float* X, const float* y, const int32_t* row_idx
                           float* grad_yv, float* grad_Xv, int32_t* grad_status,
                           ladlasso_stream_t stream);
 
+/* ladlasso_fit_batched without a caller workspace.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they fit -- a plugin inside a framework that owns all
+ * device allocations, or a serving loop that must not call cudaMalloc (which
+ * may synchronise the device) once it runs.  Same arguments, outputs, method
+ * and per-fit status as ladlasso_fit_batched; dims->workspace and
+ * dims->workspace_bytes are ignored.  The library allocates nothing: its
+ * scratch is one fixed 32 MiB device array inside the library, which every
+ * GPU that loads the library holds until the process exits.  A problem set
+ * whose scratch, 256 + (total_rows + 4*B) * round_up(P_cols, 4) * 4 bytes,
+ * exceeds 32 MiB is rejected with LADLASSO_ERR_NOMEM before any launch.
+ * The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls on a device share the array and it keeps the last call's
+ * contents: each call clears its control words itself, and calls whose
+ * kernels overlap on the GPU (e.g. on two streams) race on the array --
+ * serialise them. */
+int ladlasso_fit_batched_noalloc(const float* X, const float* y, const int32_t* row_idx,
+                                 const int64_t* offsets, const float* lambdas,
+                                 float* b_out, float* obj_out, const ladlasso_dims* dims,
+                                 ladlasso_stream_t stream);
+
 /* Human-readable name of a ladlasso_status value. */
 const char* ladlasso_status_string(int status);
 

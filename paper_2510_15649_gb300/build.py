@@ -20,7 +20,7 @@ OUT = os.path.join(HERE, "libladlasso.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["api.cu", "fit_block.cu", "fit_thread.cu", "aux_kernels.cu", "backward.cu"]
+SOURCES = ["api.cu", "fit_block.cu", "fit_thread.cu", "aux_kernels.cu", "backward.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

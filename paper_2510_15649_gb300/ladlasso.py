@@ -48,7 +48,7 @@ class LadLassoError(RuntimeError):
 
 SYMBOLS = ["ladlasso_default_opts", "ladlasso_workspace_size", "ladlasso_lambda_max",
            "ladlasso_lambda_path", "ladlasso_fit_batched", "ladlasso_fit_batched_thread",
-           "ladlasso_fit_backward", "ladlasso_status_string"]
+           "ladlasso_fit_backward", "ladlasso_status_string", "ladlasso_fit_batched_noalloc"]
 
 
 def lib():
@@ -69,7 +69,8 @@ def lib():
     L.ladlasso_lambda_max.restype = C.c_int
     L.ladlasso_lambda_path.argtypes = [P, I32, I32, F, P, P]
     L.ladlasso_lambda_path.restype = C.c_int
-    for nm in ("ladlasso_fit_batched", "ladlasso_fit_batched_thread"):
+    for nm in ("ladlasso_fit_batched", "ladlasso_fit_batched_thread",
+               "ladlasso_fit_batched_noalloc"):
         fn = getattr(L, nm)
         fn.argtypes = [P, P, P, P, P, P, P, DP, P]
         fn.restype = C.c_int
@@ -204,6 +205,24 @@ def fit(pr: Problems, lambdas: torch.Tensor, *, b_init=None, opts: Opts | None =
     fn = lib().ladlasso_fit_batched_thread if per_thread else lib().ladlasso_fit_batched
     _check(fn(_ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), _ptr(lam.contiguous()),
               _ptr(out["b"]), _ptr(out["obj"]), C.byref(d), _stream(stream)))
+    return out
+
+
+def fit_noalloc(pr: Problems, lambdas: torch.Tensor, *, opts: Opts | None = None,
+                out: dict, stream=None) -> dict:
+    """ladlasso_fit_batched_noalloc: the fit with the library's fixed
+    scratch array instead of a workspace.  `out` holds preallocated
+    b [B,L,P], obj [B,L], status [B,L] device tensors (nothing is allocated
+    here either)."""
+    B = pr.B
+    lam = lambdas.reshape(B, -1)
+    L = int(lam.shape[1])
+    d = pr.dims(L, out["obj"], opts, status=out["status"])
+    d.workspace = None
+    d.workspace_bytes = 0
+    _check(lib().ladlasso_fit_batched_noalloc(
+        _ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), _ptr(lam),
+        _ptr(out["b"]), _ptr(out["obj"]), C.byref(d), _stream(stream)))
     return out
 
 
