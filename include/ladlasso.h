@@ -101,8 +101,10 @@ void ladlasso_default_opts(ladlasso_opts* o);
  * basis_out  [B*L*P_cols] device or NULL: the final vertex's hyperplanes
  *            (row slot index i >= 0, or -(j+1) for b_j = 0); consumed by
  *            ladlasso_fit_backward
- * counters   [B*L*4] device or NULL: sweeps, chop probes, polish steps,
- *            flags (1: CCD point optimal, 2: chop ran, 4: chop point optimal)
+ * counters   [B*L*6] device or NULL: sweeps, chop probes, polish steps,
+ *            flags (1: CCD point optimal, 2: chop ran, 4: chop point optimal),
+ *            selection passes over the rows, 1-D selections (the last two
+ *            are counted by the one-warp-per-fit path only, else 0)
  * workspace  device scratch of at least ladlasso_workspace_size(...) bytes,
  *            256-byte aligned; contents need not be initialised
  * opts     host pointer or NULL for defaults */
@@ -140,9 +142,10 @@ int ladlasso_lambda_path(const float* lmax, int32_t B, int32_t L, float ratio,
 
 /* Fit every problem along its lambda path (descending order expected;
  * each path position warm-starts from the previous solution).
- * Block-per-fit kernel: one thread block holds one fit (residual and the
- * current column in registers, selection buffers and the p x p algebra in
- * shared memory) and takes problems from a device work queue.
+ * One warp holds one fit (several independent fits per thread block; one
+ * block per fit beyond 8192 rows): residual, selection buffer and the p x p
+ * algebra in shared memory, the gathered design in the workspace; warps take
+ * problems from a device work queue.
  *   lambdas [B*L], b_out [B*L*P_cols], obj_out [B*L] device.
  * obj_out holds F at the returned b. */
 int ladlasso_fit_batched(const float* X, const float* y, const int32_t* row_idx,

@@ -19,6 +19,7 @@ constexpr int kNone = -0x40000000;
 __host__ __device__ inline int coord_code(int j) { return -j - 1; }
 
 constexpr int kMaxP = 256;  // largest supported P_cols
+constexpr int kCounters = 6;  // per-fit counters (see ladlasso_dims.counters)
 
 struct Opts {
   float tol_move;

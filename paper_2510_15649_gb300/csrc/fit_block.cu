@@ -1,60 +1,89 @@
-// Block-per-fit kernel: one thread block of G threads owns one LAD-LASSO fit
-// at a time and takes problems from a device work queue (persistent grid).
+// Batched fit kernel: a "group" of G threads owns one LAD-LASSO fit at a
+// time and takes problems from a device work queue (persistent grid).
+//   G = 32   one warp per fit, NW independent warps per block, no block
+//            barriers; each 1-D step is one fused pass over the rows (below)
+//   G > 32   one block per fit (long problems); keys staged in shared memory
+//            and narrowed level by level with block barriers
 //
-// Per fit (rows i < n distributed cyclically: thread t owns i = t + k*G):
-//   registers  r[K]   residual y - X b of the thread's rows
-//              xw[K]  the current column x_ij (CCD) or edge slope v_i (polish)
-//   shared     breakpoint keys/weights of the current 1-D problem (selection
-//              buffer), the coefficient vector and the p x p basis algebra
-//   global     the problem's design gathered column-major (workspace), so a
-//              column read is one coalesced sweep
+// Per fit:
+//   shared   residual r (n floats), a selection buffer of breakpoints, the
+//            coefficient vector and the p x p basis algebra of the polish
+//   global   the problem's design gathered column-major (workspace), so a
+//            column read is one coalesced sweep (L2-resident per fit)
 //
-// Method, per lambda of the path (paper: Sections 3.3-3.5):
+// Method, per lambda of the path (paper, Sections 3.3-3.5):
 //   1. cyclical coordinate descent, each axis step the exact 1-D minimiser:
 //      the weighted median of z_i = b_j + r_i / x_ij (weights |x_ij|) and 0
-//      (weight lambda), found by sample-bracketed selection, not a sort;
+//      (weight lambda);
 //   2. if the CCD fixed point is not optimal: ternary chop along the axis
 //      of largest |b_k|, each probe a CCD restricted to the other axes,
 //      with range extension; then CCD again;
 //   3. exact polish: edge line searches between vertices (each again a
 //      weighted median) until the optimality multipliers certify the vertex.
+//
+// Weighted median on one warp (G = 32): the target is the smallest key z*
+// with W(key <= z*) >= W/2.  A pass computes every row's key on the fly,
+// classifies it against a window [lo, hi] (weight below, weight inside,
+// count inside) and compacts only the keys inside into a small shared
+// buffer.  The window for an axis step is centred on the current b_j with
+// the width of that axis' last move, so near convergence one pass holding a
+// handful of keys decides the step.  A miss shrinks the open interval known
+// to hold z* and draws the next window from 32 sampled keys in it; every
+// pass either finishes or strictly shrinks that interval.  Sums are per-lane
+// in row order then warp butterflies: deterministic for a given problem.
 #include "common.cuh"
 
 namespace ll {
 namespace {
 
 constexpr float kInf = INFINITY;
-constexpr int kSampM = 3;  // sample-bracket half-width (in samples)
-constexpr int kU = 4;      // elements per thread per compaction chunk
+constexpr int kSampM = 3;      // bracket half-width (samples) on buffer levels
+constexpr int kWinM = 4;       // bracket half-width (samples) for pass windows
+constexpr int kU = 4;          // elements per thread per compaction chunk
+constexpr int kBufCap = 512;   // selection buffer of the one-warp path
+constexpr int kMaxPasses = 64; // cap on fused passes per 1-D step
+constexpr int kAxis = 0, kEdge = 1;
 
-// Uniform per-block state, resident in shared memory.
+// Uniform per-group state, resident in shared memory.
 struct St {
-  // arrays carved from dynamic shared memory
-  float* rr;                           // residual [cap]
-  float* ck; float* cw; int* cid;     // selection buffer [cap]
-  float* bv; float* bbest; float* dv; float* mu; float* tv; float* hv;  // [P]
+  float* rr;                           // residual [ncap]
+  float* ck; float* cw; int* cid;      // selection buffer [cap]
+  float* bv; float* bbest; float* dv; float* mu; float* tv; float* hv; float* dl;  // [P]
   float* Bm;                           // [P*P]
   float* red2;                         // [W*P]
   int* code; int* phan; int* piv; int* perm; int* pcol;  // [P]
+  float* sk; float* sw; int* sid;      // special breakpoints [P+1]
   unsigned* mask;                      // basis-row bitmap [maskw]
   float* redf; int* redi;              // reductions [W*16]
   float* sampk; float* sampw;          // [32]
   int cap, maskw;
-  // the problem
   const FitArgs* a;
   const float* Xq;   // gathered design (column j at Xq + j*ld)
   const float* yq;   // targets
-  int n, p, ld, nspec;
-  float lam;
+  const float* colp; // current column (axis steps)
+  int n, p, ld, nspec, qcode;
+  float lam, bj;
   // broadcast slots
   float lo, hi, acc, wpart, half, zstar, above;
   int part, m, owner, q, flag, iter, first;
+  // fused-pass results
+  float p_wl, p_wi, p_wt, p_amin;
+  int p_cnt;
+  // per-fit counters
+  int passes, selects, sel_fail;
 };
+
+template <int G> __device__ __forceinline__ int gtid() { return G == 32 ? (threadIdx.x & 31) : threadIdx.x; }
+template <int G> __device__ __forceinline__ int gwarp() { return G == 32 ? 0 : (threadIdx.x >> 5); }
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 template <int G>
 __device__ __forceinline__ void gsync() {
   if (G == 32) __syncwarp(); else __syncthreads();
 }
+
+__device__ __forceinline__ float next_up(float v) { return v == -kInf ? v : nextafterf(v, kInf); }
+__device__ __forceinline__ float next_down(float v) { return v == kInf ? v : nextafterf(v, -kInf); }
 
 // Deterministic group reductions: warp butterflies, then warps combined in a
 // fixed order.  NS float sums, NM float mins, NI int sums, NJ int mins.
@@ -76,7 +105,7 @@ __device__ __forceinline__ void reduce(St& s, float (&fs)[NS], float (&mn)[NM], 
     mi[e] = v;
   }
   if (W == 1) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = lane_id(), warp = gwarp<G>();
   __syncthreads();
   if (lane == 0) {
 #pragma unroll
@@ -128,7 +157,7 @@ __device__ __forceinline__ float gsum2(St& s, float a, float b, float& bsum) {
 template <int G>
 __device__ __forceinline__ int gscan(St& s, int cnt, int& total) {
   constexpr int W = G / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = lane_id(), warp = gwarp<G>();
   int inc = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -150,15 +179,9 @@ __device__ __forceinline__ int gscan(St& s, int cnt, int& total) {
   return base + inc - cnt;
 }
 
-// ------------------------------------------------------------------ selection
-
-// Warp 0: sort 32 (key, weight) samples and bracket the sample position
-// where the cumulative weight reaches `frac` of the sample total.
-__device__ __noinline__ void bracket_from_samples(St& s, int ns, float frac) {
-  const int lane = threadIdx.x & 31;
-  float k = lane < ns ? s.sampk[lane] : kInf;
-  float w = lane < ns ? s.sampw[lane] : 0.f;
-  int id = lane;
+// (one warp) sort (k, w, id) ascending by (k, id) across the 32 lanes.
+__device__ __forceinline__ void warp_sort(float& k, float& w, int& id) {
+  const int lane = lane_id();
 #pragma unroll
   for (int size = 2; size <= 32; size <<= 1) {
 #pragma unroll
@@ -173,12 +196,29 @@ __device__ __noinline__ void bracket_from_samples(St& s, int ns, float frac) {
       if (take) { k = ok; w = ow; id = oi; }
     }
   }
-  float cum = w;
+}
+
+__device__ __forceinline__ float warp_incl_scan(float v) {
+  const int lane = lane_id();
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    float t = __shfl_up_sync(0xffffffffu, cum, o);
-    if (lane >= o) cum += t;
+    float t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
   }
+  return v;
+}
+
+// ------------------------------------------------------------------ buffer selection
+
+// (one warp) sort 32 (key, weight) samples and bracket the sample position
+// where the cumulative weight reaches `frac` of the sample total.
+__device__ __noinline__ void bracket_from_samples(St& s, int ns, float frac) {
+  const int lane = lane_id();
+  float k = lane < ns ? s.sampk[lane] : kInf;
+  float w = lane < ns ? s.sampw[lane] : 0.f;
+  int id = lane;
+  warp_sort(k, w, id);
+  float cum = warp_incl_scan(w);
   float tot = __shfl_sync(0xffffffffu, cum, 31);
   unsigned hit = __ballot_sync(0xffffffffu, cum >= frac * tot);
   int a = hit ? __ffs(hit) - 1 : 31;
@@ -239,32 +279,29 @@ __device__ __forceinline__ bool in_part(float kk, float lo, float hi, int part) 
   return part == 0 ? kk < lo : (part == 2 ? (kk > lo && kk < hi) : kk > hi);
 }
 
-// Weighted median of the m elements of the selection buffer: ck (keys), cw
-// (weights), ids implicit (= position) for positions < s.n on the first
-// level, else cid.  Smallest key whose cumulative weight reaches half the
-// total; ties between equal keys: the lowest id among positive weights.
-// Each level brackets the target with 32 samples, classifies every element
-// into (<lo, ==lo, (lo,hi), ==hi, >hi) with fixed-order weight sums, and
-// compacts the part holding the target in place; <= 32 elements are sorted
-// by one warp.  Result in s.zstar / s.owner (kNone: no breakpoint owner).
+// Weighted-median finish over the m0 elements of the selection buffer (ck,
+// cw, ids implicit = position below s.n when `first`, else cid).  acc0 is
+// the weight of all keys below the buffer's, half0 the target, above0 the
+// smallest key above the buffer's (for exact halves).  Each level brackets
+// the target with 32 samples, classifies the elements into (<lo, ==lo,
+// (lo,hi), ==hi, >hi) with fixed-order sums and compacts the part holding
+// the target in place; <= 32 elements are sorted by one warp.
 template <int G>
-__device__ __noinline__ void select(St& s, int m0, float cur) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float ws = 0.f;
-  for (int e = tid; e < m0; e += G) ws += s.cw[e];
-  float dummy;
-  float W = gsum2<G>(s, ws, 0.f, dummy);
-  if (!(W > 0.f)) {
+__device__ __noinline__ void select_buf(St& s, int m0, float cur, int first0, float acc0,
+                                        float half0, float above0) {
+  const int tid = gtid<G>(), lane = lane_id(), warp = gwarp<G>();
+  {
+    float ws = 0.f;
+    for (int e = tid; e < m0; e += G) ws += s.cw[e];
+    float dummy;
+    float W = gsum2<G>(s, ws, 0.f, dummy);
     gsync<G>();
-    if (tid == 0) { s.zstar = cur; s.owner = kNone; }
+    if (tid == 0) {
+      s.half = half0; s.acc = acc0; s.above = above0; s.m = m0; s.first = first0; s.flag = 0;
+      s.wpart = W;
+    }
     gsync<G>();
-    return;
   }
-  if (tid == 0) {
-    s.half = 0.5f * W; s.acc = 0.f; s.above = kInf; s.wpart = W; s.m = m0; s.first = 1;
-    s.flag = 0;
-  }
-  gsync<G>();
   const int n = s.n;
   for (;;) {
     const int m = s.m;
@@ -295,6 +332,7 @@ __device__ __noinline__ void select(St& s, int m0, float cur) {
       if (kk > hi) mn[1] = fminf(mn[1], kk);
     }
     reduce<G, 5, 2, 3, 2>(s, w5, mn, si, mi);
+    gsync<G>();
     if (tid == 0) decide(s, w5, mn, si, mi, cur);
     gsync<G>();
     if (s.flag) break;
@@ -320,7 +358,7 @@ __device__ __noinline__ void select(St& s, int m0, float cur) {
       }
       int total;
       int pos = base + gscan<G>(s, cnt, total);
-      if (G == 32) __syncwarp();
+      __syncwarp();
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
         if (bk[u] == bk[u]) { s.ck[pos] = bk[u]; s.cw[pos] = bw[u]; s.cid[pos] = bi[u]; ++pos; }
@@ -338,26 +376,8 @@ __device__ __noinline__ void select(St& s, int m0, float cur) {
     float k = lane < m ? s.ck[lane] : kInf;
     float w = lane < m ? s.cw[lane] : 0.f;
     int id = lane < m ? ((first && lane < n) ? lane : s.cid[lane]) : INT32_MAX - lane;
-#pragma unroll
-    for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        float ok = __shfl_xor_sync(0xffffffffu, k, stride);
-        float ow = __shfl_xor_sync(0xffffffffu, w, stride);
-        int oi = __shfl_xor_sync(0xffffffffu, id, stride);
-        bool up = (lane & size) == 0;
-        bool lower = (lane & stride) == 0;
-        bool other_less = ok < k || (ok == k && oi < id);
-        bool take = (lower == up) ? other_less : !other_less;
-        if (take) { k = ok; w = ow; id = oi; }
-      }
-    }
-    float cum = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      float t = __shfl_up_sync(0xffffffffu, cum, o);
-      if (lane >= o) cum += t;
-    }
+    warp_sort(k, w, id);
+    float cum = warp_incl_scan(w);
     float acc = s.acc, half = s.half;
     unsigned hit = __ballot_sync(0xffffffffu, lane < m && acc + cum >= half);
     unsigned posw = __ballot_sync(0xffffffffu, lane < m && w > 0.f);
@@ -380,18 +400,174 @@ __device__ __noinline__ void select(St& s, int m0, float cur) {
   gsync<G>();
 }
 
+// ------------------------------------------------------------------ one-warp fused selection
+
+// Breakpoint of row i for the current 1-D problem.
+//   kAxis: z = b_j + r_i / x_ij, weight |x_ij|            (axis step)
+//   kEdge: t = r_i / v_i with v_i = x_i . d, weight |v_i|  (polish edge);
+//          basis rows other than the released one stay on their hyperplanes
+template <int MODE>
+__device__ __forceinline__ void row_key(const St& s, int i, float& k, float& w) {
+  if (MODE == kAxis) {
+    const float x = s.colp[i];
+    k = x != 0.f ? s.bj + __fdividef(s.rr[i], x) : kInf;
+    w = fabsf(x);
+  } else {
+    float v = 0.f;
+    for (int c = 0; c < s.p; ++c) v += s.Xq[(int64_t)c * s.ld + i] * s.dv[c];
+    const bool inb = (s.mask[i >> 5] >> (i & 31)) & 1u;
+    if (inb && i != s.qcode) v = 0.f;
+    k = i == s.qcode ? 0.f : (v != 0.f ? __fdividef(s.rr[i], v) : kInf);
+    w = fabsf(v);
+  }
+}
+
+// (one warp) one pass over rows and specials against the window [lo, hi]:
+// weight below lo, inside, total, count inside, smallest key above hi; the
+// first kBufCap keys inside go to the buffer (row order, then specials).
+template <int MODE>
+__device__ __noinline__ void fused_pass(St& s, float lo, float hi) {
+  const int lane = lane_id();
+  const int n = s.n, m = n + s.nspec;
+  float al = 0.f, ai = 0.f, at = 0.f, amin = kInf;
+  int base = 0;
+  for (int i0 = 0; i0 < m; i0 += 32) {
+    const int e = i0 + lane;
+    float k = kInf, w = 0.f;
+    int id = 0;
+    if (e < n) {
+      row_key<MODE>(s, e, k, w);
+      id = e;
+    } else if (e < m) {
+      k = s.sk[e - n]; w = s.sw[e - n]; id = s.sid[e - n];
+    }
+    at += w;
+    const bool below = k < lo;
+    const bool in = e < m && !below && k <= hi;
+    if (below) al += w;
+    if (in) ai += w;
+    if (k > hi) amin = fminf(amin, k);
+    const unsigned msk = __ballot_sync(0xffffffffu, in);
+    const int pos = base + __popc(msk & ((1u << lane) - 1u));
+    if (in && pos < kBufCap) { s.ck[pos] = k; s.cw[pos] = w; s.cid[pos] = id; }
+    base += __popc(msk);
+  }
+  al = warp_sum(al);
+  ai = warp_sum(ai);
+  at = warp_sum(at);
+  amin = warp_min(amin);
+  __syncwarp();
+  if (lane == 0) { s.p_wl = al; s.p_wi = ai; s.p_wt = at; s.p_cnt = base; s.p_amin = amin; }
+  __syncwarp();
+}
+
+// (one warp) window inside the open interval (rl, ru) around the fraction
+// `frac` of its weight, from 32 sampled keys: strided rows, or strided
+// buffer entries when `nbuf` > 0.  Fewer than 8 samples inside: the whole
+// interval.
+template <int MODE>
+__device__ __noinline__ void region_window(St& s, float rl, float ru, float frac, int nbuf) {
+  const int lane = lane_id();
+  const int n = s.n;
+  float k = kInf, w = 0.f;
+  if (nbuf > 0) {
+    const int e = (int)(((int64_t)lane * nbuf) / 32);
+    k = s.ck[e];
+    w = s.cw[e];
+  } else if (n > 0) {
+    const int i = n >= 32 ? (int)(((int64_t)lane * n) / 32) : lane;
+    if (i < n) row_key<MODE>(s, i, k, w);
+  }
+  const bool ok = k > rl && k < ru && w > 0.f;
+  if (!ok) { k = kInf; w = 0.f; }
+  const int cnt = __popc(__ballot_sync(0xffffffffu, ok));
+  float lo = next_up(rl), hi = next_down(ru);
+  if (cnt >= 8) {
+    int id = lane;
+    warp_sort(k, w, id);  // inside samples first, in key order
+    const float cum = warp_incl_scan(w);
+    const float tot = __shfl_sync(0xffffffffu, cum, 31);
+    const unsigned hit = __ballot_sync(0xffffffffu, lane < cnt && cum >= frac * tot);
+    const int a = hit ? __ffs(hit) - 1 : cnt - 1;
+    const int ilo = a - kWinM, ihi = a + kWinM;
+    const float klo = __shfl_sync(0xffffffffu, k, max(ilo, 0));
+    const float khi = __shfl_sync(0xffffffffu, k, min(ihi, cnt - 1));
+    if (ilo >= 0) lo = klo;
+    if (ihi < cnt) hi = khi;
+  }
+  __syncwarp();
+  if (lane == 0) { s.lo = lo; s.hi = hi; }
+  __syncwarp();
+}
+
+// (one warp) weighted median of the current 1-D problem (rows via row_key,
+// specials in sk/sw/sid).  With `prior`, the first window is [lo0, hi0].
+// Result in s.zstar / s.owner.
+template <int MODE>
+__device__ __noinline__ void select_fused(St& s, float cur, bool prior, float lo0, float hi0) {
+  const int lane = lane_id();
+  float rl = -kInf, ru = kInf;  // open interval known to hold the target
+  float wrl = 0.f, wru = -1.f;  // weight of keys <= rl, < ru
+  float lo = lo0, hi = hi0;
+  if (!prior) {
+    region_window<MODE>(s, rl, ru, 0.5f, 0);
+    lo = s.lo; hi = s.hi;
+  }
+  float half = -1.f;
+  if (lane == 0) s.selects++;
+  for (int it = 0; it < kMaxPasses; ++it) {
+    fused_pass<MODE>(s, lo, hi);
+    if (lane == 0) s.passes++;
+    const float wl = s.p_wl, wi = s.p_wi, wt = s.p_wt;
+    const int cnt = s.p_cnt;
+    if (half < 0.f) {
+      if (!(wt > 0.f)) {
+        __syncwarp();
+        if (lane == 0) { s.zstar = cur; s.owner = kNone; }
+        __syncwarp();
+        return;
+      }
+      half = 0.5f * wt;
+      wru = wt;
+    }
+    if (half <= wl) {                       // target below the window
+      ru = lo; wru = wl;
+      region_window<MODE>(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
+    } else if (half > wl + wi) {            // target above the window
+      rl = hi; wrl = wl + wi;
+      region_window<MODE>(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
+    } else if (cnt <= kBufCap) {            // target inside, all keys buffered
+      select_buf<32>(s, cnt, cur, 0, wl, half, s.p_amin);
+      return;
+    } else {                                // inside but too many keys: narrow
+      rl = next_down(lo); ru = next_up(hi); wrl = wl; wru = wl + wi;
+      region_window<MODE>(s, rl, ru, (half - wl) / fmaxf(wi, 1e-30f), kBufCap);
+      if (s.lo == lo && s.hi == hi) {
+        // no narrower window from the samples (keys tie at the ends): finish
+        // on the buffered keys, which begin the window in row order
+        select_buf<32>(s, kBufCap, cur, 0, wl, half, s.p_amin);
+        return;
+      }
+    }
+    lo = s.lo; hi = s.hi;
+  }
+  __syncwarp();
+  if (lane == 0) { s.zstar = cur; s.owner = kNone; s.sel_fail = 1; }
+  __syncwarp();
+}
+
 // ------------------------------------------------------------------ warp-0 algebra
 
-// (warp 0) normal of constraint `cd` into v[0..p)
+// (one warp) normal of constraint `cd` into v[0..p)
 __device__ __forceinline__ void normal_to(St& s, int cd, float* v) {
-  const int lane = threadIdx.x & 31;
+  const int lane = lane_id();
   for (int c = lane; c < s.p; c += 32)
     v[c] = cd >= 0 ? s.Xq[(int64_t)c * s.ld + cd] : (c == -cd - 1 ? 1.f : 0.f);
 }
 
-// (warp 0) try to add constraint cd to the echelon rows Bm[0..m)
+// (one warp) try to add constraint cd to the echelon rows Bm[0..m)
 __device__ __noinline__ bool try_add(St& s, int cd, int m) {
-  const int lane = threadIdx.x & 31, p = s.p;
+  const int lane = lane_id(), p = s.p;
   float* v = s.tv;
   normal_to(s, cd, v);
   __syncwarp();
@@ -424,10 +600,10 @@ __device__ __noinline__ bool try_add(St& s, int cd, int m) {
   return true;
 }
 
-// (warp 0) basis at a CCD fixed point: the hyperplanes the axis steps landed
-// on (kept when independent), completed with coordinate hyperplanes.
+// (one warp) basis at a CCD fixed point: the hyperplanes the axis steps
+// landed on (kept when independent), completed with coordinate hyperplanes.
 __device__ __noinline__ void build_basis(St& s) {
-  const int lane = threadIdx.x & 31, p = s.p;
+  const int lane = lane_id(), p = s.p;
   int m = 0;
   for (int pass = 0; pass < 2; ++pass) {
     for (int j = 0; j < p && m < p; ++j) {
@@ -456,9 +632,9 @@ __device__ __noinline__ void build_basis(St& s) {
   }
 }
 
-// (warp 0) LU with partial pivoting of Bm in place; perm[k] = original row.
+// (one warp) LU with partial pivoting of Bm in place; perm[k] = original row.
 __device__ __noinline__ bool lu(St& s) {
-  const int lane = threadIdx.x & 31, p = s.p;
+  const int lane = lane_id(), p = s.p;
   float* B = s.Bm;
   for (int c = lane; c < p; c += 32) s.perm[c] = c;
   float amax = 0.f;
@@ -497,9 +673,9 @@ __device__ __noinline__ bool lu(St& s) {
   return true;
 }
 
-// (warp 0) solve B x = rhs, rhs in x (overwritten), with the LU in Bm.
+// (one warp) solve B x = rhs, rhs in x (overwritten), with the LU in Bm.
 __device__ __noinline__ void lu_solve(St& s, float* x) {
-  const int lane = threadIdx.x & 31, p = s.p;
+  const int lane = lane_id(), p = s.p;
   const float* B = s.Bm;
   float* t = s.tv;
   for (int c = lane; c < p; c += 32) t[c] = x[s.perm[c]];
@@ -520,9 +696,9 @@ __device__ __noinline__ void lu_solve(St& s, float* x) {
   __syncwarp();
 }
 
-// (warp 0) solve B^T x = rhs with the LU (B = P^T L U).
+// (one warp) solve B^T x = rhs with the LU (B = P^T L U).
 __device__ __noinline__ void lu_solve_t(St& s, float* x) {
-  const int lane = threadIdx.x & 31, p = s.p;
+  const int lane = lane_id(), p = s.p;
   const float* B = s.Bm;
   float* t = s.tv;
   for (int c = lane; c < p; c += 32) t[c] = x[c];
@@ -543,10 +719,10 @@ __device__ __noinline__ void lu_solve_t(St& s, float* x) {
   __syncwarp();
 }
 
-// (warp 0) form the basis matrix, factor it and snap b onto the basis
+// (one warp) form the basis matrix, factor it and snap b onto the basis
 // hyperplanes (phantom coordinates keep their value).  Sets s.flag.
 __device__ __noinline__ void snap(St& s) {
-  const int lane = threadIdx.x & 31, p = s.p;
+  const int lane = lane_id(), p = s.p;
   for (int k = 0; k < p; ++k) normal_to(s, s.code[k], s.Bm + k * p);
   for (int k = lane; k < p; k += 32) {
     int cd = s.code[k];
@@ -565,12 +741,12 @@ __device__ __noinline__ void snap(St& s) {
   __syncwarp();
 }
 
-// (warp 0) multipliers from the column sums in red2, pick the most violated
-// basis hyperplane, and (if stepping) the edge direction dv.
+// (one warp) multipliers from the column sums in red2, pick the most
+// violated basis hyperplane, and (if stepping) the edge direction dv.
 template <int G>
 __device__ __noinline__ void multipliers(St& s, bool step) {
   constexpr int W = G / 32;
-  const int lane = threadIdx.x & 31, p = s.p;
+  const int lane = lane_id(), p = s.p;
   const float lam = s.lam;
   for (int c = lane; c < p; c += 32) {
     float g = 0.f;
@@ -610,10 +786,9 @@ __device__ __noinline__ void multipliers(St& s, bool step) {
   }
 }
 
-// (thread 0) coordinate breakpoints of the edge line search, appended to the
-// selection buffer after the n rows.  Returns their count.
+// (thread 0) coordinate breakpoints of the edge line search into sk/sw/sid.
 __device__ __noinline__ int edge_specials(St& s, int q) {
-  const int p = s.p, n = s.n;
+  const int p = s.p;
   int ns = 0;
   for (int c = 0; c < p; ++c) {
     int kk = -1;
@@ -621,21 +796,20 @@ __device__ __noinline__ int edge_specials(St& s, int q) {
     if (kk >= 0 && kk != q) continue;  // other basis coordinates stay at 0
     float dc = s.dv[c];
     if (kk == q && !s.phan[q]) {
-      s.ck[n + ns] = 0.f; s.cw[n + ns] = s.lam * fabsf(dc); s.cid[n + ns] = coord_code(c); ++ns;
+      s.sk[ns] = 0.f; s.sw[ns] = s.lam * fabsf(dc); s.sid[ns] = coord_code(c); ++ns;
     } else if (dc != 0.f) {
-      s.ck[n + ns] = -s.bv[c] / dc; s.cw[n + ns] = s.lam * fabsf(dc); s.cid[n + ns] = coord_code(c); ++ns;
+      s.sk[ns] = -s.bv[c] / dc; s.sw[ns] = s.lam * fabsf(dc); s.sid[ns] = coord_code(c); ++ns;
     }
   }
   return ns;
 }
 
 // ------------------------------------------------------------------ row passes
-// The residual lives in shared memory (s.rr); threads stride over rows.
 
 template <int G>
 __device__ __forceinline__ void recompute_r(St& s) {
   const int n = s.n, p = s.p, ld = s.ld;
-  for (int i = threadIdx.x; i < n; i += G) {
+  for (int i = gtid<G>(); i < n; i += G) {
     float v = s.yq[i];
     for (int c = 0; c < p; ++c) v -= s.Xq[(int64_t)c * ld + i] * s.bv[c];
     s.rr[i] = v;
@@ -645,13 +819,41 @@ __device__ __forceinline__ void recompute_r(St& s) {
 template <int G>
 __device__ __forceinline__ float objective(St& s) {
   float a = 0.f;
-  for (int i = threadIdx.x; i < s.n; i += G) a += fabsf(s.rr[i]);
+  for (int i = gtid<G>(); i < s.n; i += G) a += fabsf(s.rr[i]);
   float b = 0.f;
-  if (threadIdx.x < 32)
-    for (int c = threadIdx.x; c < s.p; c += 32) b += fabsf(s.bv[c]);
+  if (gwarp<G>() == 0)
+    for (int c = lane_id(); c < s.p; c += 32) b += fabsf(s.bv[c]);
   float bs;
   float as = gsum2<G>(s, a, b, bs);
   return as + s.lam * bs;
+}
+
+// Block path: write the breakpoints of all rows (and the specials after
+// them) into the buffer, then select over the buffer.
+template <int G, int MODE>
+__device__ __forceinline__ void select_staged(St& s, float cur) {
+  const int n = s.n;
+  for (int i = gtid<G>(); i < n; i += G) {
+    float k, w;
+    row_key<MODE>(s, i, k, w);
+    s.ck[i] = k;
+    s.cw[i] = w;
+  }
+  for (int e = gtid<G>(); e < s.nspec; e += G) {
+    s.ck[n + e] = s.sk[e]; s.cw[n + e] = s.sw[e]; s.cid[n + e] = s.sid[e];
+  }
+  gsync<G>();
+  float ws = 0.f;
+  for (int e = gtid<G>(); e < n + s.nspec; e += G) ws += s.cw[e];
+  float dummy;
+  const float W = gsum2<G>(s, ws, 0.f, dummy);
+  gsync<G>();
+  if (!(W > 0.f)) {
+    if (gtid<G>() == 0) { s.zstar = cur; s.owner = kNone; }
+    gsync<G>();
+    return;
+  }
+  select_buf<G>(s, n + s.nspec, cur, 1, 0.f, 0.5f * W, kInf);
 }
 
 // Exact minimisation along axis j (Section 3.3): the weighted median of
@@ -662,24 +864,30 @@ __device__ __noinline__ float axis_update(St& s, int j) {
   const int n = s.n;
   const float* col = s.Xq + (int64_t)j * s.ld;
   const float bj = s.bv[j];
-  for (int i = threadIdx.x; i < n; i += G) {
-    float x = col[i];
-    s.ck[i] = x != 0.f ? bj + __fdividef(s.rr[i], x) : kInf;
-    s.cw[i] = fabsf(x);
-  }
-  const int ns = s.lam > 0.f ? 1 : 0;
-  if (threadIdx.x == 0 && ns) { s.ck[n] = 0.f; s.cw[n] = s.lam; s.cid[n] = coord_code(j); }
   gsync<G>();
-  select<G>(s, n + ns, bj);
+  if (gtid<G>() == 0) {
+    s.colp = col;
+    s.bj = bj;
+    s.nspec = s.lam > 0.f ? 1 : 0;
+    s.sk[0] = 0.f; s.sw[0] = s.lam; s.sid[0] = coord_code(j);
+  }
+  gsync<G>();
+  if (G == 32) {
+    const float dl = s.dl[j];
+    select_fused<kAxis>(s, bj, true, bj - dl, bj + dl);
+  } else {
+    select_staged<G, kAxis>(s, bj);
+  }
   const float z = s.zstar;
   const int own = s.owner;
   const float d = z - bj;
   if (d != 0.f)
-    for (int i = threadIdx.x; i < n; i += G) s.rr[i] -= col[i] * d;
+    for (int i = gtid<G>(); i < n; i += G) s.rr[i] -= col[i] * d;
   gsync<G>();
-  if (threadIdx.x == 0) {
+  if (gtid<G>() == 0) {
     s.bv[j] = z;
     s.piv[j] = own == kNone ? -2 : (own < 0 ? -1 : own);
+    s.dl[j] = fmaxf(2.f * fabsf(d), 1e-5f * fmaxf(1.f, fabsf(z)));
   }
   gsync<G>();
   return d;
@@ -709,10 +917,10 @@ __device__ __forceinline__ float probe(St& s, int k, float t, float& best_f, int
   const float d = t - s.bv[k];
   if (d != 0.f) {
     const float* col = s.Xq + (int64_t)k * s.ld;
-    for (int i = threadIdx.x; i < s.n; i += G) s.rr[i] -= col[i] * d;
+    for (int i = gtid<G>(); i < s.n; i += G) s.rr[i] -= col[i] * d;
   }
   gsync<G>();
-  if (threadIdx.x == 0) s.bv[k] = t;
+  if (gtid<G>() == 0) s.bv[k] = t;
   gsync<G>();
   int sw = ccd<G>(s, k, s.a->o.probe_max_sweeps);
   sweeps += sw < 0 ? -sw : sw;
@@ -720,7 +928,7 @@ __device__ __forceinline__ float probe(St& s, int k, float t, float& best_f, int
   float f = objective<G>(s);
   if (f < best_f) {
     best_f = f;
-    for (int c = threadIdx.x; c < s.p; c += G) s.bbest[c] = s.bv[c];
+    for (int c = gtid<G>(); c < s.p; c += G) s.bbest[c] = s.bv[c];
   }
   gsync<G>();
   return f;
@@ -734,7 +942,7 @@ __device__ __noinline__ void chop(St& s, int k, int& sweeps, int& probes) {
   const Opts& o = s.a->o;
   const float f0 = objective<G>(s);
   float best_f = f0;
-  for (int c = threadIdx.x; c < s.p; c += G) s.bbest[c] = s.bv[c];
+  for (int c = gtid<G>(); c < s.p; c += G) s.bbest[c] = s.bv[c];
   gsync<G>();
   const float c0 = s.bv[k];
   const float scale = fmaxf(1.f, fabsf(c0));
@@ -764,7 +972,7 @@ __device__ __noinline__ void chop(St& s, int k, int& sweeps, int& probes) {
     else if (g1 > g2) lo = m1;
     else { lo = m1; hi = m2; }
   }
-  for (int c = threadIdx.x; c < s.p; c += G) s.bv[c] = s.bbest[c];
+  for (int c = gtid<G>(); c < s.p; c += G) s.bv[c] = s.bbest[c];
   gsync<G>();
   recompute_r<G>(s);
   gsync<G>();
@@ -773,7 +981,7 @@ __device__ __noinline__ void chop(St& s, int k, int& sweeps, int& probes) {
 // Exact polish from the current basis (code/phan); max_piv = 0 only tests.
 template <int G>
 __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonunique) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = gtid<G>(), lane = lane_id(), warp = gwarp<G>();
   const int n = s.n, p = s.p, ld = s.ld;
   int it = 0;
   *is_opt = 0;
@@ -805,20 +1013,13 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     if (q < 0) { *is_opt = 1; *nonunique = s.iter; break; }
     if (it >= max_piv) break;
     // edge line search: breakpoints of t -> F(b + t d)
-    const int qcode = s.code[q];
-    for (int i = tid; i < n; i += G) {
-      float v = 0.f;
-      for (int c = 0; c < p; ++c) v += s.Xq[(int64_t)c * ld + i] * s.dv[c];
-      bool inb = (s.mask[i >> 5] >> (i & 31)) & 1u;
-      if (inb && i != qcode) v = 0.f;  // other basis rows stay on their hyperplanes
-      s.ck[i] = i == qcode ? 0.f : (v != 0.f ? __fdividef(s.rr[i], v) : kInf);
-      s.cw[i] = fabsf(v);
+    if (tid == 0) {
+      s.qcode = s.code[q];
+      s.nspec = edge_specials(s, q);
     }
-    if (tid == 0) s.m = edge_specials(s, q);
     gsync<G>();
-    const int ns = s.m;
-    gsync<G>();
-    select<G>(s, n + ns, 0.f);
+    if (G == 32) select_fused<kEdge>(s, 0.f, false, 0.f, 0.f);
+    else select_staged<G, kEdge>(s, 0.f);
     const float ts = s.zstar;
     const int own = s.owner;
     if (own == kNone) break;  // flat along the edge (cannot happen when F decreases)
@@ -836,26 +1037,31 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
 
 // ------------------------------------------------------------------ one problem
 
+__device__ __forceinline__ void write_fit(const FitArgs& A, int64_t f, int status, float F,
+                                          const int (&cnt)[kCounters]) {
+  A.obj_out[f] = F;
+  if (A.status) A.status[f] = status;
+  if (A.counters)
+    for (int e = 0; e < kCounters; ++e) A.counters[f * kCounters + e] = cnt[e];
+}
+
 template <int G>
 __device__ __forceinline__ void write_bad_path(St& s, int q) {
   const FitArgs& A = *s.a;
+  const int zero[kCounters] = {0, 0, 0, 0, 0, 0};
   for (int l = 0; l < A.L; ++l) {
     int64_t f = (int64_t)q * A.L + l;
-    for (int c = threadIdx.x; c < A.P; c += G) {
+    for (int c = gtid<G>(); c < A.P; c += G) {
       A.b_out[f * A.P + c] = 0.f;
       if (A.basis_out) A.basis_out[f * A.P + c] = coord_code(c);
     }
-    if (threadIdx.x == 0) {
-      A.obj_out[f] = 0.f;
-      if (A.status) A.status[f] = kFitBadInput;
-      if (A.counters) for (int e = 0; e < 4; ++e) A.counters[f * 4 + e] = 0;
-    }
+    if (gtid<G>() == 0) write_fit(A, f, kFitBadInput, 0.f, zero);
   }
 }
 
 template <int G>
 __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
-  const int tid = threadIdx.x;
+  const int tid = gtid<G>();
   const FitArgs& A = *s.a;
   int64_t o0 = 0;
   int n = 0, p = 0;
@@ -882,115 +1088,127 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
     reduce<G, 1, 1, 1, 1>(s, f, m, si, mi);
     ok = ok && si[0] == 0;
   }
-  __syncthreads();
+  gsync<G>();
   if (!ok) { write_bad_path<G>(s, q); return; }
   if (tid == 0) {
     s.n = n; s.p = p; s.ld = ld;
     s.Xq = Xw; s.yq = A.y + o0;
   }
-  __syncthreads();
+  gsync<G>();
   for (int c = tid; c < p; c += G) s.bv[c] = A.b_init ? A.b_init[(int64_t)q * A.P + c] : 0.f;
-  __syncthreads();
+  gsync<G>();
   recompute_r<G>(s);
-  __syncthreads();
+  gsync<G>();
   for (int l = 0; l < A.L; ++l) {
     const int64_t f = (int64_t)q * A.L + l;
     const float lraw = A.lambdas[f];
     if (!(lraw >= 0.f) || !isfinite(lraw)) {
+      const int zero[kCounters] = {0, 0, 0, 0, 0, 0};
       for (int c = tid; c < A.P; c += G) {
         A.b_out[f * A.P + c] = 0.f;
         if (A.basis_out) A.basis_out[f * A.P + c] = coord_code(c);
       }
-      if (tid == 0) {
-        A.obj_out[f] = 0.f;
-        if (A.status) A.status[f] = kFitBadInput;
-        if (A.counters) for (int e = 0; e < 4; ++e) A.counters[f * 4 + e] = 0;
-      }
+      if (tid == 0) write_fit(A, f, kFitBadInput, 0.f, zero);
       continue;
     }
-    if (tid == 0) s.lam = fmaxf(lraw, A.o.lambda_min_floor);
-    for (int c = tid; c < p; c += G) s.piv[c] = -2;
-    __syncthreads();
+    if (tid == 0) {
+      s.lam = fmaxf(lraw, A.o.lambda_min_floor);
+      s.passes = 0; s.selects = 0; s.sel_fail = 0;
+    }
+    for (int c = tid; c < p; c += G) {
+      s.piv[c] = -2;
+      // axis windows for the new lambda: moves are a fraction of |b_j|
+      s.dl[c] = fmaxf(0.25f * fabsf(s.bv[c]), 1e-5f);
+    }
+    gsync<G>();
     int status = kFitOk, sweeps = 0, probes = 0, pivots = 0, flags = 0;
     int sw = ccd<G>(s, -1, A.o.max_sweeps);
     sweeps += sw < 0 ? -sw : sw;
     if (sw < 0) status |= kFitMaxIters;
     int is_opt = 0, nonu = 0;
-    if (tid < 32) build_basis(s);
-    __syncthreads();
+    if (gwarp<G>() == 0) build_basis(s);
+    gsync<G>();
     polish<G>(s, 0, &is_opt, &nonu);
     if (is_opt) flags |= 1;
     if (!is_opt && A.o.chop && p >= 2) {
       // Section 3.4: any axis will do; take the largest |b_k|
       int kax = 0;
       for (int c = 1; c < p; ++c) if (fabsf(s.bv[c]) > fabsf(s.bv[kax])) kax = c;
-      __syncthreads();
+      gsync<G>();
       flags |= 2;
       chop<G>(s, kax, sweeps, probes);
       for (int c = tid; c < p; c += G) s.piv[c] = -2;
-      __syncthreads();
+      gsync<G>();
       sw = ccd<G>(s, -1, A.o.max_sweeps);
       sweeps += sw < 0 ? -sw : sw;
-      if (tid < 32) build_basis(s);
-      __syncthreads();
+      if (gwarp<G>() == 0) build_basis(s);
+      gsync<G>();
       polish<G>(s, 0, &is_opt, &nonu);
       if (is_opt) flags |= 4;
     }
     if (!is_opt && A.o.polish) {
-      if (tid < 32) build_basis(s);
-      __syncthreads();
+      if (gwarp<G>() == 0) build_basis(s);
+      gsync<G>();
       const int mp = A.o.max_pivots > 0 ? A.o.max_pivots : 4 * p + 64;
       pivots = polish<G>(s, mp, &is_opt, &nonu);
       if (!is_opt) status |= kFitMaxIters;
     }
     if (is_opt && nonu) status |= kFitNonunique;
+    if (s.sel_fail) status |= kFitMaxIters;
     const float F = objective<G>(s);
     for (int c = tid; c < A.P; c += G) {
       A.b_out[f * A.P + c] = c < p ? s.bv[c] : 0.f;
       if (A.basis_out) A.basis_out[f * A.P + c] = c < p ? s.code[c] : coord_code(c);
     }
     if (tid == 0) {
-      A.obj_out[f] = F;
-      if (A.status) A.status[f] = status;
-      if (A.counters) {
-        A.counters[f * 4 + 0] = sweeps;
-        A.counters[f * 4 + 1] = probes;
-        A.counters[f * 4 + 2] = pivots;
-        A.counters[f * 4 + 3] = flags;
-      }
+      const int cnt[kCounters] = {sweeps, probes, pivots, flags, s.passes, s.selects};
+      write_fit(A, f, status, F, cnt);
     }
-    __syncthreads();
+    gsync<G>();
   }
 }
 
-// Shared-memory bytes for a block of G threads, row capacity ncap, P columns.
+// Shared-memory bytes of one group: G threads, row capacity ncap, P columns.
 template <int G>
-size_t smem_bytes(int ncap, int P) {
+__host__ __device__ size_t group_smem_bytes(int ncap, int P) {
   constexpr int W = G / 32;
-  size_t cap = (size_t)ncap + P + 1;
-  size_t words = 4 * cap + 6 * (size_t)P + (size_t)P * P + (size_t)W * P + 5 * (size_t)P +
-                 (size_t)ncap / 32 + 1 + 2 * (size_t)W * 16 + 64;
-  return words * 4 + 16;
+  size_t cap = G == 32 ? (size_t)kBufCap : (size_t)ncap + P + 1;
+  // one warp: the basis matrix overlays the selection buffer (never live
+  // together: the polish rebuilds it after every edge line search)
+  size_t sel_bm = G == 32 ? (3 * cap > (size_t)P * P ? 3 * cap : (size_t)P * P)
+                          : 3 * cap + (size_t)P * P;
+  size_t words = (size_t)ncap + sel_bm + 7 * (size_t)P + (size_t)W * P +
+                 5 * (size_t)P + 3 * ((size_t)P + 1) + (size_t)ncap / 32 + 1 +
+                 2 * (size_t)W * 16 + 64;
+  return ((words * 4 + 15) / 16) * 16;
 }
 
 template <int G>
 __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   constexpr int W = G / 32;
-  s.cap = ncap + P + 1;
+  s.cap = G == 32 ? kBufCap : ncap + P + 1;
   s.maskw = ncap / 32 + 1;
   float* f = reinterpret_cast<float*>(raw);
-  s.rr = f; f += s.cap;
+  s.rr = f; f += ncap;
+  float* sel = f;
   s.ck = f; f += s.cap;
   s.cw = f; f += s.cap;
   s.cid = reinterpret_cast<int*>(f); f += s.cap;
+  if (G == 32) {
+    s.Bm = sel;  // overlay (see group_smem_bytes)
+    if (P * P > 3 * s.cap) f = sel + P * P;
+  } else {
+    s.Bm = f; f += P * P;
+  }
   s.bv = f; f += P; s.bbest = f; f += P; s.dv = f; f += P;
-  s.mu = f; f += P; s.tv = f; f += P; s.hv = f; f += P;
-  s.Bm = f; f += P * P;
+  s.mu = f; f += P; s.tv = f; f += P; s.hv = f; f += P; s.dl = f; f += P;
   s.red2 = f; f += W * P;
   int* ip = reinterpret_cast<int*>(f);
   s.code = ip; ip += P; s.phan = ip; ip += P; s.piv = ip; ip += P; s.perm = ip; ip += P;
   s.pcol = ip; ip += P;
   f = reinterpret_cast<float*>(ip);
+  s.sk = f; f += P + 1; s.sw = f; f += P + 1;
+  s.sid = reinterpret_cast<int*>(f); f += P + 1;
   s.mask = reinterpret_cast<unsigned*>(f); f += s.maskw;
   s.redf = f; f += W * 16;
   s.redi = reinterpret_cast<int*>(f); f += W * 16;
@@ -998,76 +1216,86 @@ __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   s.sampw = f; f += 32;
 }
 
-template <int G>
-__global__ void __launch_bounds__(G) fit_block_kernel(FitArgs args, int ncap) {
+template <int G, int NW>
+__global__ void __launch_bounds__(G * NW) fit_block_kernel(FitArgs args, int ncap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ St s;
+  __shared__ St sarr[NW];
   __shared__ FitArgs A;
-  if (threadIdx.x == 0) {
-    A = args;
-    carve<G>(s, smem_raw, ncap, args.P);
-    s.a = &A;
+  const int grp = threadIdx.x / G;
+  if (threadIdx.x == 0) A = args;
+  __syncthreads();
+  if (gtid<G>() == 0) {
+    carve<G>(sarr[grp], smem_raw + (size_t)grp * group_smem_bytes<G>(ncap, args.P), ncap, args.P);
+    sarr[grp].a = &A;
   }
   __syncthreads();
+  St& s = sarr[grp];
   for (;;) {
-    if (threadIdx.x == 0) s.q = atomicAdd(A.queue, 1);
-    __syncthreads();
+    if (gtid<G>() == 0) s.q = atomicAdd(A.queue, 1);
+    gsync<G>();
     const int q = s.q;
-    __syncthreads();
+    gsync<G>();
     if (q >= A.B) break;
     run_problem<G>(s, q, ncap);
-    __syncthreads();
+    gsync<G>();
   }
 }
 
-template <int G>
+template <int G, int NW>
 cudaError_t launch_variant(const FitArgs& a, cudaStream_t st, int num_sms, int ncap) {
-  size_t smem = smem_bytes<G>(ncap, a.P);
-  auto kern = fit_block_kernel<G>;
+  size_t smem = group_smem_bytes<G>(ncap, a.P) * NW;
+  auto kern = fit_block_kernel<G, NW>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * NW, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  int grid = per_sm * num_sms;
-  if (grid > a.B) grid = a.B;
+  int64_t grid = (int64_t)per_sm * num_sms;
+  int64_t need = ((int64_t)a.B + NW - 1) / NW;
+  if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  kern<<<grid, G, smem, st>>>(a, ncap);
+  kern<<<(int)grid, G * NW, smem, st>>>(a, ncap);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-// Largest row capacity a block of G threads can hold with P columns in the
-// shared memory one block may use (227 KB).
+// Largest row capacity one group of G threads can hold with P columns in
+// the shared memory one block may use (227 KB).
 int fit_block_max_rows(int G, int P) {
   const size_t limit = 227 * 1024;
   int lo = 0, hi = 1 << 16;
   while (lo < hi) {
     int mid = (lo + hi + 1) / 2;
-    size_t b = G == 32 ? smem_bytes<32>(mid, P) : G == 64 ? smem_bytes<64>(mid, P)
-             : G == 128 ? smem_bytes<128>(mid, P) : smem_bytes<256>(mid, P);
+    size_t b = G == 32 ? group_smem_bytes<32>(mid, P) : G == 64 ? group_smem_bytes<64>(mid, P)
+             : G == 128 ? group_smem_bytes<128>(mid, P) : group_smem_bytes<256>(mid, P);
     if (b <= limit) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
 
-// Default block size for a problem set: more threads for longer problems.
-int fit_block_group(int n_max) {
-  if (n_max <= 256) return 32;
-  if (n_max <= 1024) return 64;
-  return 128;
-}
+// Default group size for a problem set: one warp per fit while its rows fit
+// a warp's share of shared memory, else a block per fit.
+int fit_block_group(int n_max) { return n_max <= 8192 ? 32 : 128; }
 
 cudaError_t launch_fit_block(const FitArgs& a, cudaStream_t st, int num_sms, int G) {
   int ncap = (a.n_max + 31) & ~31;
   if (ncap < 32) ncap = 32;
   switch (G) {
-    case 32: return launch_variant<32>(a, st, num_sms, ncap);
-    case 64: return launch_variant<64>(a, st, num_sms, ncap);
-    case 128: return launch_variant<128>(a, st, num_sms, ncap);
-    case 256: return launch_variant<256>(a, st, num_sms, ncap);
+    case 32: {
+      // as many warps per block as shared memory allows, up to 8
+      const size_t per = group_smem_bytes<32>(ncap, a.P);
+      const size_t limit = 227 * 1024;
+      int nw = (int)(limit / (per ? per : 1));
+      if (nw >= 8) return launch_variant<32, 8>(a, st, num_sms, ncap);
+      if (nw >= 4) return launch_variant<32, 4>(a, st, num_sms, ncap);
+      if (nw >= 2) return launch_variant<32, 2>(a, st, num_sms, ncap);
+      return launch_variant<32, 1>(a, st, num_sms, ncap);
+    }
+    case 64: return launch_variant<64, 1>(a, st, num_sms, ncap);
+    case 128: return launch_variant<128, 1>(a, st, num_sms, ncap);
+    case 256: return launch_variant<256, 1>(a, st, num_sms, ncap);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -378,7 +378,7 @@ struct TFit {
       }
       A.obj_out[f] = 0.f;
       if (A.status) A.status[f] = kFitBadInput;
-      if (A.counters) for (int e = 0; e < 4; ++e) A.counters[f * 4 + e] = 0;
+      if (A.counters) for (int e = 0; e < kCounters; ++e) A.counters[f * kCounters + e] = 0;
     }
   }
 
@@ -396,7 +396,7 @@ struct TFit {
         }
         A.obj_out[f] = 0.f;
         if (A.status) A.status[f] = kFitBadInput;
-        if (A.counters) for (int e = 0; e < 4; ++e) A.counters[f * 4 + e] = 0;
+        if (A.counters) for (int e = 0; e < kCounters; ++e) A.counters[f * kCounters + e] = 0;
         continue;
       }
       lam = fmaxf(lraw, A.o.lambda_min_floor);
@@ -436,10 +436,12 @@ struct TFit {
       A.obj_out[f] = F;
       if (A.status) A.status[f] = status;
       if (A.counters) {
-        A.counters[f * 4 + 0] = sweeps;
-        A.counters[f * 4 + 1] = probes;
-        A.counters[f * 4 + 2] = pivots;
-        A.counters[f * 4 + 3] = flags;
+        A.counters[f * kCounters + 0] = sweeps;
+        A.counters[f * kCounters + 1] = probes;
+        A.counters[f * kCounters + 2] = pivots;
+        A.counters[f * kCounters + 3] = flags;
+        A.counters[f * kCounters + 4] = 0;
+        A.counters[f * kCounters + 5] = 0;
       }
     }
   }
