@@ -181,7 +181,7 @@ def main():
     ws = ll.workspace(pr, L)
     out = dict(b=torch.empty((B, L, pr.P), device=dev), obj=torch.empty((B, L), device=dev),
                status=torch.empty((B, L), dtype=torch.int32, device=dev),
-               counters=torch.empty((B, L, 6), dtype=torch.int32, device=dev))
+               counters=torch.empty((B, L, 8), dtype=torch.int32, device=dev))
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 

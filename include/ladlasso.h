@@ -101,10 +101,11 @@ void ladlasso_default_opts(ladlasso_opts* o);
  * basis_out  [B*L*P_cols] device or NULL: the final vertex's hyperplanes
  *            (row slot index i >= 0, or -(j+1) for b_j = 0); consumed by
  *            ladlasso_fit_backward
- * counters   [B*L*6] device or NULL: sweeps, chop probes, polish steps,
+ * counters   [B*L*8] device or NULL: sweeps, chop probes, polish steps,
  *            flags (1: CCD point optimal, 2: chop ran, 4: chop point optimal),
- *            selection passes over the rows, 1-D selections (the last two
- *            are counted by the one-warp-per-fit path only, else 0)
+ *            selection passes over the rows, 1-D selections, kilocycles in
+ *            descent + chop, kilocycles in basis/polish work (the last four
+ *            are counted by the batched kernel only, else 0)
  * workspace  device scratch of at least ladlasso_workspace_size(...) bytes,
  *            256-byte aligned; contents need not be initialised
  * opts     host pointer or NULL for defaults */
@@ -199,8 +200,9 @@ int ladlasso_fit_backward(const float* X, const float* y, const int32_t* row_idx
  * dims->workspace_bytes are ignored.  The library allocates nothing: its
  * scratch is one fixed 32 MiB device array inside the library, which every
  * GPU that loads the library holds until the process exits.  A problem set
- * whose scratch, 256 + (total_rows + 4*B) * round_up(P_cols, 4) * 4 bytes,
- * exceeds 32 MiB is rejected with LADLASSO_ERR_NOMEM before any launch.
+ * whose scratch, 256 + round_up(4*B, 256) + (total_rows + 4*B) *
+ * round_up(P_cols, 4) * 4 bytes, exceeds 32 MiB is rejected with
+ * LADLASSO_ERR_NOMEM before any launch.
  * The first call on a device looks up the array's device address (with
  * that device current); make that first call before any stream capture.
  * All calls on a device share the array and it keeps the last call's

@@ -12,6 +12,8 @@ cudaError_t launch_fit_thread(const FitArgs& a, cudaStream_t st, int num_sms);
 cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t total_rows, int* ctrl,
                                     cudaStream_t st);
 cudaError_t launch_lambda_max(const FitArgs& a, float* lmax, cudaStream_t st, int num_sms);
+cudaError_t launch_order(const int64_t* offsets, const int32_t* p, int P, int B, int* order,
+                         cudaStream_t st);
 cudaError_t launch_lambda_path(const float* lmax, int B, int L, float ratio, float* lam,
                                cudaStream_t st);
 cudaError_t launch_backward(const FitArgs& a, int pos, const float* b_out, const int32_t* basis,
@@ -46,7 +48,7 @@ bool ws_layout(int32_t B, int32_t P, int64_t total_rows, WsLayout* w) {
   size_t P4 = ((size_t)P + 3) & ~(size_t)3;
   size_t rows = (size_t)total_rows + 4 * (size_t)B;
   w->ctrl = 0;
-  w->xg = 256;
+  w->xg = ll::ws_xg_offset(B);
   size_t xg_bytes = align256(rows * P4 * sizeof(float));
   w->scratch = w->xg + xg_bytes;
   // thread-per-fit scratch: per slot (key, weight, id, residual) for
@@ -109,6 +111,7 @@ int prepare(const float* X, const float* y, const int32_t* row_idx, const int64_
   a->counters = d->counters;
   unsigned char* ws = (unsigned char*)d->workspace;
   a->queue = (int*)(ws + w.ctrl);
+  a->order = (int*)(ws + ll::ws_order_offset());
   a->Xg = (float*)(ws + w.xg);
   a->scratch = ws + w.scratch;
   a->B = d->B;
@@ -199,6 +202,8 @@ static int fit_common(const float* X, const float* y, const int32_t* row_idx,
   if (rc != LADLASSO_OK) return rc;
   int sms = num_sms();
   if (sms <= 0) return LADLASSO_ERR_CUDA;
+  if (!per_thread && ll::launch_order(a.offsets, a.p, a.P, a.B, a.order, st) != cudaSuccess)
+    return LADLASSO_ERR_CUDA;
   cudaError_t e = per_thread ? ll::launch_fit_thread(a, st, sms)
                              : ll::launch_fit_block(a, st, sms, G);
   return cuda_status(e);

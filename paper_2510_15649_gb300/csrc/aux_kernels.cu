@@ -59,6 +59,38 @@ __global__ void lambda_max_kernel(FitArgs a, float* lmax) {
   }
 }
 
+// Work order for the persistent fit kernels: problems sorted by decreasing
+// estimated cost n * p (longest first keeps the tail short).  One block;
+// counting sort over logarithmic cost buckets (order within a bucket is
+// arbitrary and does not affect any result).
+constexpr int kBuckets = 128;
+__device__ __forceinline__ int cost_bucket(const int64_t* offsets, const int32_t* p, int P, int q) {
+  int64_t n = offsets[q + 1] - offsets[q];
+  int pq = p ? p[q] : P;
+  if (n < 0) n = 0;
+  if (pq < 0) pq = 0;
+  float cost = (float)n * (float)pq;
+  int b = (int)(3.f * log2f(1.f + cost));
+  return b < 0 ? 0 : (b >= kBuckets ? kBuckets - 1 : b);
+}
+
+__global__ void order_kernel(const int64_t* offsets, const int32_t* p, int P, int B, int* order) {
+  __shared__ int hist[kBuckets];
+  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < B; q += blockDim.x) atomicAdd(&hist[cost_bucket(offsets, p, P, q)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;  // largest bucket first
+    for (int b = kBuckets - 1; b >= 0; --b) { int c = hist[b]; hist[b] = run; run += c; }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < B; q += blockDim.x) {
+    int pos = atomicAdd(&hist[cost_bucket(offsets, p, P, q)], 1);
+    order[pos] = q;
+  }
+}
+
 __global__ void lambda_path_kernel(const float* lmax, int B, int L, float ratio, float* lam) {
   int64_t total = (int64_t)B * L;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -77,6 +109,13 @@ cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t total
   int blocks = (B + 1 + threads - 1) / threads;
   if (blocks > 4096) blocks = 4096;
   validate_offsets_kernel<<<blocks, threads, 0, st>>>(offsets, B, total_rows, ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order(const int64_t* offsets, const int32_t* p, int P, int B, int* order,
+                         cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  order_kernel<<<1, 1024, 0, st>>>(offsets, p, P, B, order);
   return cudaGetLastError();
 }
 

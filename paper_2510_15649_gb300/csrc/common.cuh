@@ -19,7 +19,7 @@ constexpr int kNone = -0x40000000;
 __host__ __device__ inline int coord_code(int j) { return -j - 1; }
 
 constexpr int kMaxP = 256;  // largest supported P_cols
-constexpr int kCounters = 6;  // per-fit counters (see ladlasso_dims.counters)
+constexpr int kCounters = 8;  // per-fit counters (see ladlasso_dims.counters)
 
 struct Opts {
   float tol_move;
@@ -51,7 +51,8 @@ struct FitArgs {
   int32_t* basis_out;
   int32_t* counters;
   float* Xg;        // workspace: gathered column-major designs
-  int* queue;       // workspace: work counter
+  int* queue;       // workspace: work counter (queue[0]) and offsets flag (queue[1])
+  int* order;       // workspace: problems in decreasing estimated cost (block path)
   unsigned char* scratch;  // workspace: per-fit scratch (thread-per-fit kernel)
   int B, P, L, n_max;
   int64_t ldX, rows_X, total_rows;
@@ -61,6 +62,7 @@ struct FitArgs {
 
 // Workspace layout (bytes, 256-aligned sections):
 //   [0, 256)            control words (work counters)
+//   order               B ints: problems in decreasing estimated cost
 //   Xg                  (total_rows + 4 B) * P4 floats: problem q's column j
 //                       starts at xg_base(q) + j * ld(n_q), ld = round_up(n,4)
 //   thread scratch      per-slot and per-problem scratch for the
@@ -69,6 +71,38 @@ __host__ __device__ inline int64_t xg_base(int64_t off_q, int q, int P4) {
   return (off_q + 4 * (int64_t)q) * P4;
 }
 __host__ __device__ inline int64_t xg_ld(int n) { return ((int64_t)n + 3) & ~(int64_t)3; }
+__host__ __device__ inline size_t ws_order_offset() { return 256; }
+__host__ __device__ inline size_t ws_xg_offset(int B) {
+  return 256 + ((4 * (size_t)B + 255) & ~(size_t)255);
+}
+
+// Shared-window accessors: keep hot loops on the shared-memory pipe when the
+// pointer has travelled through generic code.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ float lds_f(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts_f(uint32_t a, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void sts_i(uint32_t a, int v) {
+  asm volatile("st.shared.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+// 16-byte global -> shared copy that bypasses registers (completes
+// asynchronously; wait with cp_async_wait_all).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

@@ -40,9 +40,11 @@ constexpr float kInf = INFINITY;
 constexpr int kSampM = 3;      // bracket half-width (samples) on buffer levels
 constexpr int kWinM = 4;       // bracket half-width (samples) for pass windows
 constexpr int kU = 4;          // elements per thread per compaction chunk
-constexpr int kBufCap = 512;   // selection buffer of the one-warp path
+constexpr int kBufCap = 256;   // selection buffer of the one-warp path
 constexpr int kMaxPasses = 64; // cap on fused passes per 1-D step
 constexpr int kAxis = 0, kEdge = 1;
+// dynamic shared memory one block may take: 227 KB less the static state
+constexpr size_t kDynSmemLimit = 227 * 1024 - 8 * 1024;
 
 // Uniform per-group state, resident in shared memory.
 struct St {
@@ -59,6 +61,8 @@ struct St {
   int cap, maskw;
   const FitArgs* a;
   const float* Xq;   // gathered design (column j at Xq + j*ld)
+  float* cb[2];      // one warp: double-buffered copy of the current column
+  int cur;           // buffer holding the column of the current axis step
   const float* yq;   // targets
   const float* colp; // current column (axis steps)
   int n, p, ld, nspec, qcode;
@@ -288,20 +292,14 @@ __device__ __forceinline__ bool in_part(float kk, float lo, float hi, int part) 
 // the target in place; <= 32 elements are sorted by one warp.
 template <int G>
 __device__ __noinline__ void select_buf(St& s, int m0, float cur, int first0, float acc0,
-                                        float half0, float above0) {
+                                        float half0, float above0, float wbuf) {
   const int tid = gtid<G>(), lane = lane_id(), warp = gwarp<G>();
-  {
-    float ws = 0.f;
-    for (int e = tid; e < m0; e += G) ws += s.cw[e];
-    float dummy;
-    float W = gsum2<G>(s, ws, 0.f, dummy);
-    gsync<G>();
-    if (tid == 0) {
-      s.half = half0; s.acc = acc0; s.above = above0; s.m = m0; s.first = first0; s.flag = 0;
-      s.wpart = W;
-    }
-    gsync<G>();
+  gsync<G>();
+  if (tid == 0) {
+    s.half = half0; s.acc = acc0; s.above = above0; s.m = m0; s.first = first0; s.flag = 0;
+    s.wpart = wbuf;  // only steers the sample brackets
   }
+  gsync<G>();
   const int n = s.n;
   for (;;) {
     const int m = s.m;
@@ -370,34 +368,53 @@ __device__ __noinline__ void select_buf(St& s, int m0, float cur, int first0, fl
     gsync<G>();
   }
   if (!s.flag && warp == 0) {
-    // at most 32 candidates: one warp sorts by (key, id) and scans
+    // at most 32 candidates, one per lane.  For each, the weight of all
+    // candidates with key <= its key (one pass over the candidates, read as
+    // shared-memory broadcasts); the target key is the smallest key whose
+    // cumulative weight (plus acc) reaches half.
     const int m = s.m;
     const int first = s.first;
-    float k = lane < m ? s.ck[lane] : kInf;
-    float w = lane < m ? s.cw[lane] : 0.f;
-    int id = lane < m ? ((first && lane < n) ? lane : s.cid[lane]) : INT32_MAX - lane;
-    warp_sort(k, w, id);
-    float cum = warp_incl_scan(w);
-    float acc = s.acc, half = s.half;
-    unsigned hit = __ballot_sync(0xffffffffu, lane < m && acc + cum >= half);
-    unsigned posw = __ballot_sync(0xffffffffu, lane < m && w > 0.f);
-    int c = hit ? __ffs(hit) - 1 : (posw ? 31 - __clz(posw) : 0);
-    float z = __shfl_sync(0xffffffffu, k, c);
-    unsigned eq = __ballot_sync(0xffffffffu, lane < m && k == z);
-    unsigned eqw = __ballot_sync(0xffffffffu, lane < m && k == z && w > 0.f);
-    int last = 31 - __clz(eq);
-    int own_lane = eqw ? __ffs(eqw) - 1 : c;
-    int own = __shfl_sync(0xffffffffu, id, own_lane);
-    float cum_g = acc + __shfl_sync(0xffffffffu, cum, last);
-    float next_in = __shfl_sync(0xffffffffu, k, min(last + 1, 31));
+    const float* __restrict__ ck = s.ck;
+    const float* __restrict__ cw = s.cw;
+    const bool have = lane < m;
+    const float k = have ? ck[lane] : kInf;
+    const float w = have ? cw[lane] : 0.f;
+    const int id = have ? ((first && lane < n) ? lane : s.cid[lane]) : INT32_MAX;
+    float cle = 0.f;
+    for (int j = 0; j < m; ++j) {
+      const float kj = ck[j];
+      if (kj <= k) cle += cw[j];
+    }
+    const float acc = s.acc, half = s.half;
+    const bool cand = have && acc + cle >= half;
+    float z = warp_min(cand ? k : kInf);
+    if (!(z < kInf)) {
+      // rounding left every cumulative below half: the largest positive-weight key
+      float zmax = have && w > 0.f ? k : -kInf;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+      z = zmax;
+    }
+    int own = have && k == z && w > 0.f ? id : INT32_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) own = min(own, __shfl_xor_sync(0xffffffffu, own, o));
+    const float cum_g = acc + __shfl_sync(0xffffffffu, cle, __ffs(__ballot_sync(0xffffffffu, have && k == z)) - 1);
+    const float next_in = warp_min(have && k > z ? k : kInf);
     if (lane == 0) {
-      float next = (last + 1 < m) ? next_in : s.above;
-      if (m > 0 && z < kInf) finalize(s, z, own, cum_g, next, cur);
-      else { s.flag = 1; s.zstar = cur; s.owner = kNone; }  // rounding left nothing: no move
+      const float next = fminf(next_in, s.above);
+      if (m > 0 && z < kInf && z > -kInf) finalize(s, z, own == INT32_MAX ? kNone : own, cum_g, next, cur);
+      else { s.flag = 1; s.zstar = cur; s.owner = kNone; }  // nothing selectable: no move
     }
     __syncwarp();
   }
   gsync<G>();
+}
+
+__device__ __forceinline__ float xval(const St& s, int c, int i) {
+  return s.Xq[(int64_t)c * s.ld + i];
+}
+__device__ __forceinline__ const float* colptr(const St& s, int c) {
+  return s.Xq + (int64_t)c * s.ld;
 }
 
 // ------------------------------------------------------------------ one-warp fused selection
@@ -414,7 +431,10 @@ __device__ __forceinline__ void row_key(const St& s, int i, float& k, float& w) 
     w = fabsf(x);
   } else {
     float v = 0.f;
-    for (int c = 0; c < s.p; ++c) v += s.Xq[(int64_t)c * s.ld + i] * s.dv[c];
+    for (int c = 0; c < s.p; ++c) {
+      const float dc = s.dv[c];
+      if (dc != 0.f) v += xval(s, c, i) * dc;  // d is zero on basis coordinates
+    }
     const bool inb = (s.mask[i >> 5] >> (i & 31)) & 1u;
     if (inb && i != s.qcode) v = 0.f;
     k = i == s.qcode ? 0.f : (v != 0.f ? __fdividef(s.rr[i], v) : kInf);
@@ -423,41 +443,113 @@ __device__ __forceinline__ void row_key(const St& s, int i, float& k, float& w) 
 }
 
 // (one warp) one pass over rows and specials against the window [lo, hi]:
-// weight below lo, inside, total, count inside, smallest key above hi; the
-// first kBufCap keys inside go to the buffer (row order, then specials).
+// weight below lo, weight at or below hi (accumulated on its own, so that
+// the same set of keys always sums to the same value whichever window
+// selects it), total, count inside, smallest key above hi; the first
+// kBufCap keys inside go to the buffer (row order, then specials).  Rows
+// are taken kPassU per lane at a time so their loads overlap.
+constexpr int kPassU = 8;
+
+// The buffer pointers are passed in registers (restrict-qualified): going
+// through the shared state struct would reload them after every store.
+__device__ __forceinline__ void classify_one(float* __restrict__ bk, float* __restrict__ bw,
+                                             int* __restrict__ bi, float k, float w, int id,
+                                             bool valid, float lo, float hi, float& al, float& ale,
+                                             float& at, float& amin, int& base) {
+  const int lane = lane_id();
+  at += w;
+  if (k < lo) al += w;
+  if (k <= hi) ale += w;
+  const bool in = valid && k >= lo && k <= hi;
+  if (k > hi) amin = fminf(amin, k);
+  const unsigned msk = __ballot_sync(0xffffffffu, in);
+  const int pos = base + __popc(msk & ((1u << lane) - 1u));
+  if (in && pos < kBufCap) { bk[pos] = k; bw[pos] = w; bi[pos] = id; }
+  base += __popc(msk);
+}
+
+// Axis-step rows: z = b_j + r_i / x_ij, weight |x_ij|.  Full batches of
+// 32 * kPassU rows run without bounds checks; the compaction code runs only
+// when some lane of the warp holds a key inside the window.
+// Axis-step rows from shared memory (the column buffer and the residual):
+// z = b_j + r_i / x_ij, weight |x_ij|.  Full batches of 32 * kPassU rows run
+// without bounds checks; the compaction code runs only when some lane of
+// the warp holds a key inside the window.
+__device__ __forceinline__ void axis_rows(uint32_t col_s, uint32_t rr_s, float bj, int n,
+                                          float lo, float hi, uint32_t bk_s, uint32_t bw_s,
+                                          uint32_t bi_s, float& al, float& ale, float& at,
+                                          float& amin, int& base) {
+  const int lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int i0 = 0; i0 < n; i0 += 32 * kPassU) {
+    float xv[kPassU], rv[kPassU];
+#pragma unroll
+    for (int u = 0; u < kPassU; ++u) {
+      const int e = i0 + u * 32 + lane;
+      xv[u] = e < n ? lds_f(col_s + 4u * e) : 0.f;
+      rv[u] = e < n ? lds_f(rr_s + 4u * e) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kPassU; ++u) {
+      if (i0 + u * 32 >= n) break;  // uniform
+      const int e = i0 + u * 32 + lane;
+      const float x = xv[u];  // zero beyond n: no weight, key +inf
+      const float w = fabsf(x);
+      const float k = x != 0.f ? bj + __fdividef(rv[u], x) : kInf;
+      at += w;
+      al += k < lo ? w : 0.f;
+      ale += k <= hi ? w : 0.f;
+      amin = k > hi ? fminf(amin, k) : amin;
+      const bool in = e < n && k >= lo && k <= hi;
+      const unsigned msk = __ballot_sync(0xffffffffu, in);
+      if (msk) {
+        const int pos = base + __popc(msk & lt);
+        if (in && pos < kBufCap) {
+          sts_f(bk_s + 4u * pos, k);
+          sts_f(bw_s + 4u * pos, w);
+          sts_i(bi_s + 4u * pos, e);
+        }
+        base += __popc(msk);
+      }
+    }
+  }
+}
+
 template <int MODE>
 __device__ __noinline__ void fused_pass(St& s, float lo, float hi) {
   const int lane = lane_id();
-  const int n = s.n, m = n + s.nspec;
-  float al = 0.f, ai = 0.f, at = 0.f, amin = kInf;
+  const int n = s.n, nspec = s.nspec;
+  float* __restrict__ bk = s.ck;
+  float* __restrict__ bw = s.cw;
+  int* __restrict__ bi = s.cid;
+  float al = 0.f, ale = 0.f, at = 0.f, amin = kInf;
   int base = 0;
-  for (int i0 = 0; i0 < m; i0 += 32) {
-    const int e = i0 + lane;
-    float k = kInf, w = 0.f;
-    int id = 0;
-    if (e < n) {
-      row_key<MODE>(s, e, k, w);
-      id = e;
-    } else if (e < m) {
-      k = s.sk[e - n]; w = s.sw[e - n]; id = s.sid[e - n];
+  if (MODE == kAxis) {
+    axis_rows(smem_u32(s.colp), smem_u32(s.rr), s.bj, n, lo, hi, smem_u32(bk), smem_u32(bw),
+              smem_u32(bi), al, ale, at, amin, base);
+  } else {
+    for (int i0 = 0; i0 < n; i0 += 32) {
+      const int e = i0 + lane;
+      float k = kInf, w = 0.f;
+      if (e < n) row_key<MODE>(s, e, k, w);
+      classify_one(bk, bw, bi, k, w, e, e < n, lo, hi, al, ale, at, amin, base);
     }
-    at += w;
-    const bool below = k < lo;
-    const bool in = e < m && !below && k <= hi;
-    if (below) al += w;
-    if (in) ai += w;
-    if (k > hi) amin = fminf(amin, k);
-    const unsigned msk = __ballot_sync(0xffffffffu, in);
-    const int pos = base + __popc(msk & ((1u << lane) - 1u));
-    if (in && pos < kBufCap) { s.ck[pos] = k; s.cw[pos] = w; s.cid[pos] = id; }
-    base += __popc(msk);
+  }
+  const float* __restrict__ sk = s.sk;
+  const float* __restrict__ sw = s.sw;
+  const int* __restrict__ sid = s.sid;
+  for (int j0 = 0; j0 < nspec; j0 += 32) {
+    const int e = j0 + lane;
+    const bool v = e < nspec;
+    classify_one(bk, bw, bi, v ? sk[e] : kInf, v ? sw[e] : 0.f, v ? sid[e] : 0, v, lo, hi, al,
+                 ale, at, amin, base);
   }
   al = warp_sum(al);
-  ai = warp_sum(ai);
+  ale = warp_sum(ale);
   at = warp_sum(at);
   amin = warp_min(amin);
   __syncwarp();
-  if (lane == 0) { s.p_wl = al; s.p_wi = ai; s.p_wt = at; s.p_cnt = base; s.p_amin = amin; }
+  if (lane == 0) { s.p_wl = al; s.p_wi = ale; s.p_wt = at; s.p_cnt = base; s.p_amin = amin; }
   __syncwarp();
 }
 
@@ -518,7 +610,7 @@ __device__ __noinline__ void select_fused(St& s, float cur, bool prior, float lo
   for (int it = 0; it < kMaxPasses; ++it) {
     fused_pass<MODE>(s, lo, hi);
     if (lane == 0) s.passes++;
-    const float wl = s.p_wl, wi = s.p_wi, wt = s.p_wt;
+    const float wl = s.p_wl, wle = s.p_wi, wt = s.p_wt;
     const int cnt = s.p_cnt;
     if (half < 0.f) {
       if (!(wt > 0.f)) {
@@ -533,23 +625,24 @@ __device__ __noinline__ void select_fused(St& s, float cur, bool prior, float lo
     if (half <= wl) {                       // target below the window
       ru = lo; wru = wl;
       region_window<MODE>(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
-    } else if (half > wl + wi) {            // target above the window
-      rl = hi; wrl = wl + wi;
+    } else if (half > wle) {                // target above the window
+      rl = hi; wrl = wle;
       region_window<MODE>(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
     } else if (cnt <= kBufCap) {            // target inside, all keys buffered
-      select_buf<32>(s, cnt, cur, 0, wl, half, s.p_amin);
+      select_buf<32>(s, cnt, cur, 0, wl, half, s.p_amin, wle - wl);
       return;
     } else {                                // inside but too many keys: narrow
-      rl = next_down(lo); ru = next_up(hi); wrl = wl; wru = wl + wi;
-      region_window<MODE>(s, rl, ru, (half - wl) / fmaxf(wi, 1e-30f), kBufCap);
+      rl = next_down(lo); ru = next_up(hi); wrl = wl; wru = wle;
+      region_window<MODE>(s, rl, ru, (half - wl) / fmaxf(wle - wl, 1e-30f), kBufCap);
       if (s.lo == lo && s.hi == hi) {
         // no narrower window from the samples (keys tie at the ends): finish
         // on the buffered keys, which begin the window in row order
-        select_buf<32>(s, kBufCap, cur, 0, wl, half, s.p_amin);
+        select_buf<32>(s, kBufCap, cur, 0, wl, half, s.p_amin, wle - wl);
         return;
       }
     }
     lo = s.lo; hi = s.hi;
+    if (!(lo <= hi)) break;  // empty interval: only reachable through inconsistent input
   }
   __syncwarp();
   if (lane == 0) { s.zstar = cur; s.owner = kNone; s.sel_fail = 1; }
@@ -562,7 +655,7 @@ __device__ __noinline__ void select_fused(St& s, float cur, bool prior, float lo
 __device__ __forceinline__ void normal_to(St& s, int cd, float* v) {
   const int lane = lane_id();
   for (int c = lane; c < s.p; c += 32)
-    v[c] = cd >= 0 ? s.Xq[(int64_t)c * s.ld + cd] : (c == -cd - 1 ? 1.f : 0.f);
+    v[c] = cd >= 0 ? xval(s, c, cd) : (c == -cd - 1 ? 1.f : 0.f);
 }
 
 // (one warp) try to add constraint cd to the echelon rows Bm[0..m)
@@ -806,14 +899,68 @@ __device__ __noinline__ int edge_specials(St& s, int q) {
 
 // ------------------------------------------------------------------ row passes
 
+// r = y - X b, one column at a time, skipping zero coefficients (b is
+// sparse along most of the path); loads batched kPassU per thread.
 template <int G>
 __device__ __forceinline__ void recompute_r(St& s) {
-  const int n = s.n, p = s.p, ld = s.ld;
-  for (int i = gtid<G>(); i < n; i += G) {
-    float v = s.yq[i];
-    for (int c = 0; c < p; ++c) v -= s.Xq[(int64_t)c * ld + i] * s.bv[c];
-    s.rr[i] = v;
+  const int n = s.n, p = s.p;
+  const int t = gtid<G>();
+  const float* __restrict__ yq = s.yq;
+  const float* __restrict__ bv = s.bv;
+  float* __restrict__ rr = s.rr;
+  for (int i0 = 0; i0 < n; i0 += G * kPassU) {
+    float v[kPassU];
+#pragma unroll
+    for (int u = 0; u < kPassU; ++u) {
+      const int i = i0 + u * G + t;
+      v[u] = i < n ? yq[i] : 0.f;
+    }
+    for (int c = 0; c < p; ++c) {
+      const float b = bv[c];
+      if (b == 0.f) continue;  // uniform
+      const float* __restrict__ col = colptr(s, c);
+#pragma unroll
+      for (int u = 0; u < kPassU; ++u) {
+        const int i = i0 + u * G + t;
+        if (i < n) v[u] -= col[i] * b;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPassU; ++u) {
+      const int i = i0 + u * G + t;
+      if (i < n) rr[i] = v[u];
+    }
   }
+}
+
+// r -= d * column (global or shared), loads batched kPassU per thread.
+template <int G>
+__device__ __forceinline__ void axpy_r(St& s, const float* __restrict__ col, float d) {
+  const int n = s.n, t = gtid<G>();
+  const uint32_t rr_s = smem_u32(s.rr);
+  for (int i0 = 0; i0 < n; i0 += G * kPassU) {
+    float xv[kPassU];
+#pragma unroll
+    for (int u = 0; u < kPassU; ++u) {
+      const int i = i0 + u * G + t;
+      xv[u] = i < n ? col[i] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kPassU; ++u) {
+      const int i = i0 + u * G + t;
+      if (i < n) sts_f(rr_s + 4u * i, lds_f(rr_s + 4u * i) - xv[u] * d);
+    }
+  }
+}
+
+// (one warp) start copying column j into column buffer `buf` (16-byte
+// asynchronous copies; the gathered column is 16-byte aligned and padded
+// to a multiple of 4 floats).
+__device__ __forceinline__ void prefetch_col(St& s, int j, int buf) {
+  const float* src = s.Xq + (int64_t)j * s.ld;
+  const uint32_t dst = smem_u32(s.cb[buf]);
+  for (int q = lane_id(); q < (s.ld >> 2); q += 32) cp_async16(dst + 16u * q, src + 4 * q);
+  cp_async_commit();
 }
 
 template <int G>
@@ -853,17 +1000,23 @@ __device__ __forceinline__ void select_staged(St& s, float cur) {
     gsync<G>();
     return;
   }
-  select_buf<G>(s, n + s.nspec, cur, 1, 0.f, 0.5f * W, kInf);
+  select_buf<G>(s, n + s.nspec, cur, 1, 0.f, 0.5f * W, kInf, W);
 }
 
 // Exact minimisation along axis j (Section 3.3): the weighted median of
 // z_i = b_j + r_i / x_ij (weights |x_ij|) and 0 (weight lambda).  Returns
 // the move; records the breakpoint landed on in piv[j].
 template <int G>
-__device__ __noinline__ float axis_update(St& s, int j) {
-  const int n = s.n;
-  const float* col = s.Xq + (int64_t)j * s.ld;
+__device__ __noinline__ float axis_update(St& s, int j, int jnext) {
   const float bj = s.bv[j];
+  const float* col = colptr(s, j);
+  if (G == 32) {
+    // the column of this step was prefetched into cb[cur]; start the next
+    cp_async_wait_all();
+    __syncwarp();
+    if (jnext >= 0) prefetch_col(s, jnext, s.cur ^ 1);
+    col = s.cb[s.cur];
+  }
   gsync<G>();
   if (gtid<G>() == 0) {
     s.colp = col;
@@ -881,13 +1034,13 @@ __device__ __noinline__ float axis_update(St& s, int j) {
   const float z = s.zstar;
   const int own = s.owner;
   const float d = z - bj;
-  if (d != 0.f)
-    for (int i = gtid<G>(); i < n; i += G) s.rr[i] -= col[i] * d;
+  if (d != 0.f) axpy_r<G>(s, col, d);
   gsync<G>();
   if (gtid<G>() == 0) {
     s.bv[j] = z;
     s.piv[j] = own == kNone ? -2 : (own < 0 ? -1 : own);
     s.dl[j] = fmaxf(2.f * fabsf(d), 1e-5f * fmaxf(1.f, fabsf(z)));
+    if (G == 32) s.cur ^= 1;
   }
   gsync<G>();
   return d;
@@ -897,14 +1050,28 @@ __device__ __noinline__ float axis_update(St& s, int j) {
 template <int G>
 __device__ __noinline__ int ccd(St& s, int skip, int max_sweeps) {
   const float tol = s.a->o.tol_move;
+  const int p = s.p;
+  const int j0 = skip == 0 ? 1 : 0;  // first axis of a sweep
+  if (j0 >= p) return 1;              // nothing to move
+  if (G == 32) {
+    cp_async_wait_all();  // no copy may still target a buffer
+    __syncwarp();
+    if (lane_id() == 0) s.cur = 0;
+    __syncwarp();
+    prefetch_col(s, j0, 0);
+  }
   for (int sw = 1; sw <= max_sweeps; ++sw) {
     float mx = 0.f;
-    for (int j = 0; j < s.p; ++j) {
+    for (int j = j0; j < p; ++j) {
       if (j == skip) continue;
-      mx = fmaxf(mx, fabsf(axis_update<G>(s, j)));
+      int jn = j + 1;
+      if (jn == skip) ++jn;
+      if (jn >= p) jn = j0;  // first axis of the next sweep
+      mx = fmaxf(mx, fabsf(axis_update<G>(s, j, jn)));
     }
     float bmax = 0.f;
-    for (int c = 0; c < s.p; ++c) bmax = fmaxf(bmax, fabsf(s.bv[c]));
+    for (int c = lane_id(); c < s.p; c += 32) bmax = fmaxf(bmax, fabsf(s.bv[c]));
+    bmax = warp_max(bmax);
     if (mx <= tol * fmaxf(1.f, bmax)) return sw;
   }
   return -max_sweeps;
@@ -915,10 +1082,7 @@ template <int G>
 __device__ __forceinline__ float probe(St& s, int k, float t, float& best_f, int& sweeps,
                                        int& probes) {
   const float d = t - s.bv[k];
-  if (d != 0.f) {
-    const float* col = s.Xq + (int64_t)k * s.ld;
-    for (int i = gtid<G>(); i < s.n; i += G) s.rr[i] -= col[i] * d;
-  }
+  if (d != 0.f) axpy_r<G>(s, colptr(s, k), d);
   gsync<G>();
   if (gtid<G>() == 0) s.bv[k] = t;
   gsync<G>();
@@ -999,7 +1163,7 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     gsync<G>();
     // column sums g_c = -sum_{rows not in basis} sign(r_i) x_ic
     for (int c = 0; c < p; ++c) {
-      const float* col = s.Xq + (int64_t)c * ld;
+      const float* col = colptr(s, c);
       float a = 0.f;
       for (int i = tid; i < n; i += G)
         if (!((s.mask[i >> 5] >> (i & 31)) & 1u)) a -= fsign(s.rr[i]) * col[i];
@@ -1048,7 +1212,7 @@ __device__ __forceinline__ void write_fit(const FitArgs& A, int64_t f, int statu
 template <int G>
 __device__ __forceinline__ void write_bad_path(St& s, int q) {
   const FitArgs& A = *s.a;
-  const int zero[kCounters] = {0, 0, 0, 0, 0, 0};
+  const int zero[kCounters] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int l = 0; l < A.L; ++l) {
     int64_t f = (int64_t)q * A.L + l;
     for (int c = gtid<G>(); c < A.P; c += G) {
@@ -1103,7 +1267,7 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
     const int64_t f = (int64_t)q * A.L + l;
     const float lraw = A.lambdas[f];
     if (!(lraw >= 0.f) || !isfinite(lraw)) {
-      const int zero[kCounters] = {0, 0, 0, 0, 0, 0};
+      const int zero[kCounters] = {0, 0, 0, 0, 0, 0, 0, 0};
       for (int c = tid; c < A.P; c += G) {
         A.b_out[f * A.P + c] = 0.f;
         if (A.basis_out) A.basis_out[f * A.P + c] = coord_code(c);
@@ -1122,14 +1286,17 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
     }
     gsync<G>();
     int status = kFitOk, sweeps = 0, probes = 0, pivots = 0, flags = 0;
+    long long t_cd = 0, t_vx = 0, t0 = clock64();  // cycles: descent+chop, vertex work
     int sw = ccd<G>(s, -1, A.o.max_sweeps);
     sweeps += sw < 0 ? -sw : sw;
     if (sw < 0) status |= kFitMaxIters;
     int is_opt = 0, nonu = 0;
+    long long t1 = clock64(); t_cd += t1 - t0; t0 = t1;
     if (gwarp<G>() == 0) build_basis(s);
     gsync<G>();
     polish<G>(s, 0, &is_opt, &nonu);
     if (is_opt) flags |= 1;
+    t1 = clock64(); t_vx += t1 - t0; t0 = t1;
     if (!is_opt && A.o.chop && p >= 2) {
       // Section 3.4: any axis will do; take the largest |b_k|
       int kax = 0;
@@ -1141,6 +1308,7 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
       gsync<G>();
       sw = ccd<G>(s, -1, A.o.max_sweeps);
       sweeps += sw < 0 ? -sw : sw;
+      t1 = clock64(); t_cd += t1 - t0; t0 = t1;
       if (gwarp<G>() == 0) build_basis(s);
       gsync<G>();
       polish<G>(s, 0, &is_opt, &nonu);
@@ -1153,6 +1321,7 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
       pivots = polish<G>(s, mp, &is_opt, &nonu);
       if (!is_opt) status |= kFitMaxIters;
     }
+    t1 = clock64(); t_vx += t1 - t0;
     if (is_opt && nonu) status |= kFitNonunique;
     if (s.sel_fail) status |= kFitMaxIters;
     const float F = objective<G>(s);
@@ -1161,7 +1330,8 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
       if (A.basis_out) A.basis_out[f * A.P + c] = c < p ? s.code[c] : coord_code(c);
     }
     if (tid == 0) {
-      const int cnt[kCounters] = {sweeps, probes, pivots, flags, s.passes, s.selects};
+      const int cnt[kCounters] = {sweeps, probes, pivots, flags, s.passes, s.selects,
+                                  (int)(t_cd >> 10), (int)(t_vx >> 10)};
       write_fit(A, f, status, F, cnt);
     }
     gsync<G>();
@@ -1177,7 +1347,8 @@ __host__ __device__ size_t group_smem_bytes(int ncap, int P) {
   // together: the polish rebuilds it after every edge line search)
   size_t sel_bm = G == 32 ? (3 * cap > (size_t)P * P ? 3 * cap : (size_t)P * P)
                           : 3 * cap + (size_t)P * P;
-  size_t words = (size_t)ncap + sel_bm + 7 * (size_t)P + (size_t)W * P +
+  size_t colbuf = G == 32 ? 2 * (size_t)ncap : 0;
+  size_t words = (size_t)ncap + colbuf + sel_bm + 7 * (size_t)P + (size_t)W * P +
                  5 * (size_t)P + 3 * ((size_t)P + 1) + (size_t)ncap / 32 + 1 +
                  2 * (size_t)W * 16 + 64;
   return ((words * 4 + 15) / 16) * 16;
@@ -1190,6 +1361,8 @@ __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   s.maskw = ncap / 32 + 1;
   float* f = reinterpret_cast<float*>(raw);
   s.rr = f; f += ncap;
+  if (G == 32) { s.cb[0] = f; f += ncap; s.cb[1] = f; f += ncap; }
+  else { s.cb[0] = s.cb[1] = nullptr; }
   float* sel = f;
   s.ck = f; f += s.cap;
   s.cw = f; f += s.cap;
@@ -1219,7 +1392,7 @@ __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
 template <int G, int NW>
 __global__ void __launch_bounds__(G * NW) fit_block_kernel(FitArgs args, int ncap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ St sarr[NW];
+  __shared__ St sarr[NW];  // blockDim.x / G of them are used
   __shared__ FitArgs A;
   const int grp = threadIdx.x / G;
   if (threadIdx.x == 0) A = args;
@@ -1231,7 +1404,10 @@ __global__ void __launch_bounds__(G * NW) fit_block_kernel(FitArgs args, int nca
   __syncthreads();
   St& s = sarr[grp];
   for (;;) {
-    if (gtid<G>() == 0) s.q = atomicAdd(A.queue, 1);
+    if (gtid<G>() == 0) {
+      const int t = atomicAdd(A.queue, 1);
+      s.q = t < A.B ? A.order[t] : A.B;  // longest problems first
+    }
     gsync<G>();
     const int q = s.q;
     gsync<G>();
@@ -1241,21 +1417,22 @@ __global__ void __launch_bounds__(G * NW) fit_block_kernel(FitArgs args, int nca
   }
 }
 
+// nw groups per block (nw <= NW).
 template <int G, int NW>
-cudaError_t launch_variant(const FitArgs& a, cudaStream_t st, int num_sms, int ncap) {
-  size_t smem = group_smem_bytes<G>(ncap, a.P) * NW;
+cudaError_t launch_variant(const FitArgs& a, cudaStream_t st, int num_sms, int ncap, int nw) {
+  size_t smem = group_smem_bytes<G>(ncap, a.P) * nw;
   auto kern = fit_block_kernel<G, NW>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * NW, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * nw, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int64_t grid = (int64_t)per_sm * num_sms;
-  int64_t need = ((int64_t)a.B + NW - 1) / NW;
+  int64_t need = ((int64_t)a.B + nw - 1) / nw;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  kern<<<(int)grid, G * NW, smem, st>>>(a, ncap);
+  kern<<<(int)grid, G * nw, smem, st>>>(a, ncap);
   return cudaGetLastError();
 }
 
@@ -1264,7 +1441,7 @@ cudaError_t launch_variant(const FitArgs& a, cudaStream_t st, int num_sms, int n
 // Largest row capacity one group of G threads can hold with P columns in
 // the shared memory one block may use (227 KB).
 int fit_block_max_rows(int G, int P) {
-  const size_t limit = 227 * 1024;
+  const size_t limit = kDynSmemLimit;
   int lo = 0, hi = 1 << 16;
   while (lo < hi) {
     int mid = (lo + hi + 1) / 2;
@@ -1284,18 +1461,18 @@ cudaError_t launch_fit_block(const FitArgs& a, cudaStream_t st, int num_sms, int
   if (ncap < 32) ncap = 32;
   switch (G) {
     case 32: {
-      // as many warps per block as shared memory allows, up to 8
+      // one block per SM holding as many one-warp fits as shared memory
+      // allows (up to 16)
       const size_t per = group_smem_bytes<32>(ncap, a.P);
-      const size_t limit = 227 * 1024;
+      const size_t limit = kDynSmemLimit;
       int nw = (int)(limit / (per ? per : 1));
-      if (nw >= 8) return launch_variant<32, 8>(a, st, num_sms, ncap);
-      if (nw >= 4) return launch_variant<32, 4>(a, st, num_sms, ncap);
-      if (nw >= 2) return launch_variant<32, 2>(a, st, num_sms, ncap);
-      return launch_variant<32, 1>(a, st, num_sms, ncap);
+      if (nw > 16) nw = 16;
+      if (nw < 1) nw = 1;
+      return launch_variant<32, 16>(a, st, num_sms, ncap, nw);
     }
-    case 64: return launch_variant<64, 1>(a, st, num_sms, ncap);
-    case 128: return launch_variant<128, 1>(a, st, num_sms, ncap);
-    case 256: return launch_variant<256, 1>(a, st, num_sms, ncap);
+    case 64: return launch_variant<64, 1>(a, st, num_sms, ncap, 1);
+    case 128: return launch_variant<128, 1>(a, st, num_sms, ncap, 1);
+    case 256: return launch_variant<256, 1>(a, st, num_sms, ncap, 1);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -440,8 +440,7 @@ struct TFit {
         A.counters[f * kCounters + 1] = probes;
         A.counters[f * kCounters + 2] = pivots;
         A.counters[f * kCounters + 3] = flags;
-        A.counters[f * kCounters + 4] = 0;
-        A.counters[f * kCounters + 5] = 0;
+        for (int e = 4; e < kCounters; ++e) A.counters[f * kCounters + e] = 0;
       }
     }
   }

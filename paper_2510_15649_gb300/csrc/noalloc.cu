@@ -14,6 +14,8 @@ namespace ll {
 cudaError_t launch_fit_block(const FitArgs& a, cudaStream_t st, int num_sms, int G);
 cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t total_rows, int* ctrl,
                                     cudaStream_t st);
+cudaError_t launch_order(const int64_t* offsets, const int32_t* p, int P, int B, int* order,
+                         cudaStream_t st);
 int fit_block_group(int n_max);
 int fit_block_max_rows(int G, int P);
 }  // namespace ll
@@ -24,7 +26,7 @@ namespace {
 
 // Scratch shared by every call on a device; held by each GPU that loads the
 // library until the process exits.  Layout as in the caller workspace:
-// 256 bytes of control words, then the gathered designs.
+// 256 bytes of control words, the work order, then the gathered designs.
 constexpr size_t kScratchBytes = (size_t)32 << 20;  // 32 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -56,9 +58,9 @@ extern "C" int ladlasso_fit_batched_noalloc(const float* X, const float* y, cons
     return LADLASSO_ERR_INVALID;
   if (d->total_rows > 0 && (!y || (!X && d->rows_X > 0))) return LADLASSO_ERR_INVALID;
   if (!row_idx && d->total_rows > d->rows_X) return LADLASSO_ERR_INVALID;
-  // scratch needed: control words + gathered designs (see common.cuh)
+  // scratch needed: control words, work order, gathered designs (see common.cuh)
   const size_t P4 = ((size_t)d->P_cols + 3) & ~(size_t)3;
-  const size_t need = 256 + ((size_t)d->total_rows + 4 * (size_t)d->B) * P4 * sizeof(float);
+  const size_t need = ws_xg_offset(d->B) + ((size_t)d->total_rows + 4 * (size_t)d->B) * P4 * sizeof(float);
   if (need > kScratchBytes) return LADLASSO_ERR_NOMEM;  // problem set too large for the fixed array
   const int G = fit_block_group(d->n_max);
   if (d->n_max > fit_block_max_rows(G, d->P_cols)) return LADLASSO_ERR_NOMEM;
@@ -76,7 +78,8 @@ extern "C" int ladlasso_fit_batched_noalloc(const float* X, const float* y, cons
   a.b_out = b_out; a.obj_out = obj_out;
   a.status = d->fit_status; a.basis_out = d->basis_out; a.counters = d->counters;
   a.queue = (int*)base;
-  a.Xg = (float*)(base + 256);
+  a.order = (int*)(base + ws_order_offset());
+  a.Xg = (float*)(base + ws_xg_offset(d->B));
   a.scratch = nullptr;
   a.B = d->B; a.P = d->P_cols; a.L = d->L; a.n_max = d->n_max;
   a.ldX = d->ldX; a.rows_X = d->rows_X; a.total_rows = d->total_rows;
@@ -99,5 +102,6 @@ extern "C" int ladlasso_fit_batched_noalloc(const float* X, const float* y, cons
   if (cudaMemsetAsync(a.queue, 0, 256, st) != cudaSuccess) return LADLASSO_ERR_CUDA;
   if (launch_validate_offsets(offsets, a.B, a.total_rows, a.queue, st) != cudaSuccess)
     return LADLASSO_ERR_CUDA;
+  if (launch_order(offsets, a.p, a.P, a.B, a.order, st) != cudaSuccess) return LADLASSO_ERR_CUDA;
   return launch_fit_block(a, st, sms, G) == cudaSuccess ? LADLASSO_OK : LADLASSO_ERR_CUDA;
 }

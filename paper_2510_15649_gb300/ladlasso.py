@@ -199,7 +199,7 @@ def fit(pr: Problems, lambdas: torch.Tensor, *, b_init=None, opts: Opts | None =
         if basis:
             out["basis"] = torch.empty((B, L, P), dtype=torch.int32, device=dev)
         if counters:
-            out["counters"] = torch.empty((B, L, 6), dtype=torch.int32, device=dev)
+            out["counters"] = torch.empty((B, L, 8), dtype=torch.int32, device=dev)
     d = pr.dims(L, ws, opts, b_init=b_init, status=out["status"], basis=out.get("basis"),
                 counters=out.get("counters"))
     fn = lib().ladlasso_fit_batched_thread if per_thread else lib().ladlasso_fit_batched
