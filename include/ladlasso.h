@@ -180,7 +180,8 @@ int ladlasso_fit_batched_thread(const float* X, const float* y, const int32_t* r
  *   (per slot, so no atomics); grad_yv [total validation rows];
  *   grad_Xv [total validation rows x P_cols].
  * A problem whose vertex is not strict gets NaN gradients and status bit
- * LADLASSO_FIT_NONUNIQUE in grad_status [B] (may be NULL). */
+ * LADLASSO_FIT_NONUNIQUE in grad_status [B] (may be NULL).  val_loss [B]
+ * (may be NULL) receives the validation loss itself. */
 int ladlasso_fit_backward(const float* X, const float* y, const int32_t* row_idx,
                           const int64_t* offsets, const ladlasso_dims* dims, int32_t pos,
                           const float* b_out, const int32_t* basis_out,
@@ -189,7 +190,7 @@ int ladlasso_fit_backward(const float* X, const float* y, const int32_t* row_idx
                           int64_t total_vrows, const float* grad_up,
                           float* grad_lambda, float* grad_y, float* grad_X,
                           float* grad_yv, float* grad_Xv, int32_t* grad_status,
-                          ladlasso_stream_t stream);
+                          float* val_loss, ladlasso_stream_t stream);
 
 /* ladlasso_fit_batched without a caller workspace.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate

@@ -20,7 +20,7 @@ cudaError_t launch_backward(const FitArgs& a, int pos, const float* b_out, const
                             const float* Xv, int64_t ldXv, const float* yv, const int32_t* vrow,
                             const int64_t* voff, int64_t total_vrows, const float* gup,
                             float* glam, float* gy, float* gX, float* gyv, float* gXv,
-                            int32_t* gstat, cudaStream_t st, int num_sms);
+                            int32_t* gstat, float* vloss, cudaStream_t st, int num_sms);
 }  // namespace ll
 
 namespace {
@@ -228,7 +228,8 @@ int ladlasso_fit_backward(const float* X, const float* y, const int32_t* row_idx
                           int64_t ldXv, const float* yv, const int32_t* vrow_idx,
                           const int64_t* voffsets, int64_t total_vrows, const float* grad_up,
                           float* grad_lambda, float* grad_y, float* grad_X, float* grad_yv,
-                          float* grad_Xv, int32_t* grad_status, ladlasso_stream_t stream) {
+                          float* grad_Xv, int32_t* grad_status, float* val_loss,
+                          ladlasso_stream_t stream) {
   ll::FitArgs a;
   int rc = prepare(X, y, row_idx, offsets, dims, &a);
   if (rc != LADLASSO_OK) return rc;
@@ -243,7 +244,8 @@ int ladlasso_fit_backward(const float* X, const float* y, const int32_t* row_idx
   if (rc != LADLASSO_OK) return rc;
   return cuda_status(ll::launch_backward(a, pos, b_out, basis_out, Xv, ldXv, yv, vrow_idx,
                                          voffsets, total_vrows, grad_up, grad_lambda, grad_y,
-                                         grad_X, grad_yv, grad_Xv, grad_status, st, num_sms()));
+                                         grad_X, grad_yv, grad_Xv, grad_status, val_loss, st,
+                                         num_sms()));
 }
 
 const char* ladlasso_status_string(int status) {

@@ -33,6 +33,7 @@ struct BwdArgs {
   float* gyv;
   float* gXv;
   int32_t* gstat;
+  float* vloss;
 };
 
 __global__ void __launch_bounds__(32) backward_kernel(BwdArgs g) {
@@ -88,13 +89,16 @@ __global__ void __launch_bounds__(32) backward_kernel(BwdArgs g) {
     // validation residual signs, direct terms and g_S
     for (int a2 = lane; a2 < ns; a2 += 32) wv[a2] = 0.f;
     __syncwarp();
+    float loss = 0.f;
     for (int v = 0; v < nv; ++v) {
       int64_t row = g.vrow ? (int64_t)g.vrow[v0 + v] : v0 + v;
       const float* xr = g.Xv + row * g.ldXv;
       float s = 0.f;
       for (int c = lane; c < p; c += 32) s += xr[c] * b[c];
       s = warp_sum(s);
-      float sg = fsign(g.yv[v0 + v] - s);
+      const float rv = g.yv[v0 + v] - s;
+      float sg = fsign(rv);
+      loss += fabsf(rv);
       if (lane == 0) g.gyv[v0 + v] = up * sg;
       for (int c = lane; c < P; c += 32) g.gXv[(v0 + v) * P + c] = c < p ? -up * sg * b[c] : 0.f;
       for (int a2 = lane; a2 < ns; a2 += 32) wv[a2] -= sg * xr[S[a2]];
@@ -157,6 +161,7 @@ __global__ void __launch_bounds__(32) backward_kernel(BwdArgs g) {
     }
     __syncwarp();
     if (lane == 0) {
+      if (g.vloss) g.vloss[q] = ok ? loss : NAN;
       g.glam[q] = (ok && strict) ? 0.f : NAN;
       if (g.gstat) g.gstat[q] = !ok ? kFitBadInput : (strict ? kFitOk : kFitNonunique);
     }
@@ -173,11 +178,11 @@ cudaError_t launch_backward(const FitArgs& a, int pos, const float* b_out, const
                             const float* Xv, int64_t ldXv, const float* yv, const int32_t* vrow,
                             const int64_t* voff, int64_t total_vrows, const float* gup,
                             float* glam, float* gy, float* gX, float* gyv, float* gXv,
-                            int32_t* gstat, cudaStream_t st, int num_sms) {
+                            int32_t* gstat, float* vloss, cudaStream_t st, int num_sms) {
   BwdArgs g;
   g.a = a; g.pos = pos; g.b_out = b_out; g.basis = basis; g.Xv = Xv; g.ldXv = ldXv; g.yv = yv;
   g.vrow = vrow; g.voff = voff; g.total_vrows = total_vrows; g.gup = gup; g.glam = glam;
-  g.gy = gy; g.gX = gX; g.gyv = gyv; g.gXv = gXv; g.gstat = gstat;
+  g.gy = gy; g.gX = gX; g.gyv = gyv; g.gXv = gXv; g.gstat = gstat; g.vloss = vloss;
   int grid = a.B < num_sms * 16 ? a.B : num_sms * 16;
   if (grid < 1) grid = 1;
   backward_kernel<<<grid, 32, 0, st>>>(g);

@@ -75,7 +75,7 @@ def lib():
         fn.argtypes = [P, P, P, P, P, P, P, DP, P]
         fn.restype = C.c_int
     L.ladlasso_fit_backward.argtypes = [P, P, P, P, DP, I32, P, P, P, I64, P, P, P, I64, P,
-                                        P, P, P, P, P, P, P]
+                                        P, P, P, P, P, P, P, P]
     L.ladlasso_fit_backward.restype = C.c_int
     L.ladlasso_status_string.argtypes = [C.c_int]
     L.ladlasso_status_string.restype = C.c_char_p
@@ -229,7 +229,8 @@ def fit_noalloc(pr: Problems, lambdas: torch.Tensor, *, opts: Opts | None = None
 def fit_backward(pr: Problems, fwd: dict, pos: int, val: Problems, grad_up: torch.Tensor,
                  ws: torch.Tensor | None = None, opts: Opts | None = None, stream=None) -> dict:
     """Gradient of sum_v |y_v - x_v b| per problem at path position `pos`
-    of a forward result that carries `basis`.  Returns dict(lam [B], y, X, yv, Xv, status)."""
+    of a forward result that carries `basis`.  Returns dict(lam [B], y, X,
+    yv, Xv, status [B], loss [B])."""
     B, P = pr.B, pr.P
     L = int(fwd["b"].shape[1])
     dev = pr.X.device
@@ -239,12 +240,40 @@ def fit_backward(pr: Problems, fwd: dict, pos: int, val: Problems, grad_up: torc
              X=torch.empty((pr.y.numel(), P), dtype=torch.float32, device=dev),
              yv=torch.empty(val.y.numel(), dtype=torch.float32, device=dev),
              Xv=torch.empty((val.y.numel(), P), dtype=torch.float32, device=dev),
-             status=torch.empty(B, dtype=torch.int32, device=dev))
+             status=torch.empty(B, dtype=torch.int32, device=dev),
+             loss=torch.empty(B, dtype=torch.float32, device=dev))
     d = pr.dims(L, ws, opts)
     _check(lib().ladlasso_fit_backward(
         _ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), C.byref(d), int(pos),
         _ptr(fwd["b"]), _ptr(fwd["basis"]), _ptr(val.X), int(val.X.stride(0)), _ptr(val.y),
-        _ptr(val.row_idx), _ptr(val.offsets), int(val.y.numel()), _ptr(grad_up.contiguous()),
+        _ptr(val.row_idx), _ptr(val.offsets), int(val.y.numel()),
+        _ptr(grad_up.contiguous().float()),
         _ptr(g["lam"]), _ptr(g["y"]), _ptr(g["X"]), _ptr(g["yv"]), _ptr(g["Xv"]),
-        _ptr(g["status"]), _stream(stream)))
+        _ptr(g["status"]), _ptr(g["loss"]), _stream(stream)))
     return g
+
+
+class ValidationLoss(torch.autograd.Function):
+    """Per-problem validation LAD loss of the fit at one lambda, as a
+    differentiable function of (training y, training X rows, lambda,
+    validation y, validation X rows).
+
+    forward(X, y, lam, Xv, yv, train, val): `train` / `val` are Problems
+    whose X and y are the tensors X / y and Xv / yv; lam [B] is the lambda
+    of each problem.  Returns loss [B].  Gradients flow to y, lam, yv and,
+    per slot, to the X rows each problem uses (X must be indexed by slot:
+    row_idx None).  The fit and both passes run in the CUDA library."""
+
+    @staticmethod
+    def forward(ctx, X, y, lam, Xv, yv, train: Problems, val: Problems, opts=None):
+        fwd = fit(train, lam.reshape(-1, 1).contiguous(), basis=True, opts=opts)
+        zero = torch.zeros(train.B, dtype=torch.float32, device=X.device)
+        g = fit_backward(train, fwd, 0, val, zero)
+        ctx.train, ctx.val, ctx.fwd = train, val, fwd
+        ctx.mark_non_differentiable()
+        return g["loss"]
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        g = fit_backward(ctx.train, ctx.fwd, 0, ctx.val, grad_loss.contiguous())
+        return g["X"], g["y"], g["lam"], g["Xv"], g["yv"], None, None, None
