@@ -96,7 +96,13 @@ void ladlasso_default_opts(ladlasso_opts* o);
  * rows_X   rows of X (row_idx range check)    total_rows  offsets[B] (slots)
  * n_max    host-known bound on n_q; problems with more rows get BAD_INPUT
  * p        [B] device or NULL
- * b_init   [B*P_cols] device or NULL: warm start for path position 0
+ * n_rows   [B] device or NULL: problem q uses only the first n_rows[q]
+ *          slots of its range offsets[q] .. offsets[q+1]-1 (a count above
+ *          the range is BAD_INPUT); lets fixed-capacity slots hold problems
+ *          of any size (serving)
+ * b_init   [B*P_cols] device or NULL: warm start for path position 0 (may
+ *          alias b_out when L == 1: each problem reads its own start before
+ *          writing its result)
  * fit_status [B*L] device or NULL
  * basis_out  [B*L*P_cols] device or NULL: the final vertex's hyperplanes
  *            (row slot index i >= 0, or -(j+1) for b_j = 0); consumed by
@@ -114,6 +120,7 @@ typedef struct ladlasso_dims {
   int32_t n_max;
   int64_t ldX, rows_X, total_rows;
   const int32_t* p;
+  const int32_t* n_rows;
   const float* b_init;
   int32_t* fit_status;
   int32_t* basis_out;

@@ -12,8 +12,8 @@ cudaError_t launch_fit_thread(const FitArgs& a, cudaStream_t st, int num_sms);
 cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t total_rows, int* ctrl,
                                     cudaStream_t st);
 cudaError_t launch_lambda_max(const FitArgs& a, float* lmax, cudaStream_t st, int num_sms);
-cudaError_t launch_order(const int64_t* offsets, const int32_t* p, int P, int B, int* order,
-                         cudaStream_t st);
+cudaError_t launch_order(const int64_t* offsets, const int32_t* nr, const int32_t* p, int P, int B,
+                         int* order, cudaStream_t st);
 cudaError_t launch_lambda_path(const float* lmax, int B, int L, float ratio, float* lam,
                                cudaStream_t st);
 cudaError_t launch_backward(const FitArgs& a, int pos, const float* b_out, const int32_t* basis,
@@ -105,6 +105,7 @@ int prepare(const float* X, const float* y, const int32_t* row_idx, const int64_
   a->row_idx = row_idx;
   a->offsets = offsets;
   a->p = d->p;
+  a->n_rows = d->n_rows;
   a->b_init = d->b_init;
   a->status = d->fit_status;
   a->basis_out = d->basis_out;
@@ -202,7 +203,7 @@ static int fit_common(const float* X, const float* y, const int32_t* row_idx,
   if (rc != LADLASSO_OK) return rc;
   int sms = num_sms();
   if (sms <= 0) return LADLASSO_ERR_CUDA;
-  if (!per_thread && ll::launch_order(a.offsets, a.p, a.P, a.B, a.order, st) != cudaSuccess)
+  if (!per_thread && ll::launch_order(a.offsets, a.n_rows, a.p, a.P, a.B, a.order, st) != cudaSuccess)
     return LADLASSO_ERR_CUDA;
   cudaError_t e = per_thread ? ll::launch_fit_thread(a, st, sms)
                              : ll::launch_fit_block(a, st, sms, G);

@@ -24,14 +24,13 @@ __global__ void lambda_max_kernel(FitArgs a, float* lmax) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x / 32;
   const int* ctrl = a.queue;
   for (int q = blockIdx.x; q < a.B; q += gridDim.x) {
-    int64_t o0 = a.offsets[q];
-    int64_t o1 = a.offsets[q + 1];
+    int64_t o0 = 0, nn = 0;
     int p = a.p ? a.p[q] : a.P;
-    bool ok = ctrl[1] == 0 && o0 >= 0 && o1 >= o0 && o1 <= a.total_rows &&
-              (o1 - o0) <= (int64_t)a.n_max && p >= 1 && p <= a.P;
+    bool ok = ctrl[1] == 0 && problem_rows(a, q, o0, nn) && nn <= (int64_t)a.n_max && p >= 1 &&
+              p <= a.P;
     if (tid == 0) bad_s = ok ? 0 : 1;
     __syncthreads();
-    int n = ok ? (int)(o1 - o0) : 0;
+    int n = ok ? (int)nn : 0;
     float best = 0.f;
     for (int c = 0; c < p && ok; ++c) {
       float s = 0.f;
@@ -64,8 +63,9 @@ __global__ void lambda_max_kernel(FitArgs a, float* lmax) {
 // counting sort over logarithmic cost buckets (order within a bucket is
 // arbitrary and does not affect any result).
 constexpr int kBuckets = 128;
-__device__ __forceinline__ int cost_bucket(const int64_t* offsets, const int32_t* p, int P, int q) {
-  int64_t n = offsets[q + 1] - offsets[q];
+__device__ __forceinline__ int cost_bucket(const int64_t* offsets, const int32_t* nr,
+                                           const int32_t* p, int P, int q) {
+  int64_t n = nr ? (int64_t)nr[q] : offsets[q + 1] - offsets[q];
   int pq = p ? p[q] : P;
   if (n < 0) n = 0;
   if (pq < 0) pq = 0;
@@ -74,11 +74,12 @@ __device__ __forceinline__ int cost_bucket(const int64_t* offsets, const int32_t
   return b < 0 ? 0 : (b >= kBuckets ? kBuckets - 1 : b);
 }
 
-__global__ void order_kernel(const int64_t* offsets, const int32_t* p, int P, int B, int* order) {
+__global__ void order_kernel(const int64_t* offsets, const int32_t* nr, const int32_t* p, int P,
+                             int B, int* order) {
   __shared__ int hist[kBuckets];
   for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) hist[b] = 0;
   __syncthreads();
-  for (int q = threadIdx.x; q < B; q += blockDim.x) atomicAdd(&hist[cost_bucket(offsets, p, P, q)], 1);
+  for (int q = threadIdx.x; q < B; q += blockDim.x) atomicAdd(&hist[cost_bucket(offsets, nr, p, P, q)], 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     int run = 0;  // largest bucket first
@@ -86,7 +87,7 @@ __global__ void order_kernel(const int64_t* offsets, const int32_t* p, int P, in
   }
   __syncthreads();
   for (int q = threadIdx.x; q < B; q += blockDim.x) {
-    int pos = atomicAdd(&hist[cost_bucket(offsets, p, P, q)], 1);
+    int pos = atomicAdd(&hist[cost_bucket(offsets, nr, p, P, q)], 1);
     order[pos] = q;
   }
 }
@@ -112,10 +113,10 @@ cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t total
   return cudaGetLastError();
 }
 
-cudaError_t launch_order(const int64_t* offsets, const int32_t* p, int P, int B, int* order,
-                         cudaStream_t st) {
+cudaError_t launch_order(const int64_t* offsets, const int32_t* nr, const int32_t* p, int P, int B,
+                         int* order, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
-  order_kernel<<<1, 1024, 0, st>>>(offsets, p, P, B, order);
+  order_kernel<<<1, 1024, 0, st>>>(offsets, nr, p, P, B, order);
   return cudaGetLastError();
 }
 

@@ -43,12 +43,12 @@ __global__ void __launch_bounds__(32) backward_kernel(BwdArgs g) {
   size_t slots = (size_t)a.total_rows + (size_t)a.B * (P + 1);
   size_t slot_bytes = (slots * 16 + 255) & ~(size_t)255;
   for (int q = blockIdx.x; q < a.B; q += gridDim.x) {
-    int64_t o0 = a.offsets[q], o1 = a.offsets[q + 1];
+    int64_t o0 = 0, nn = 0;
     int64_t v0 = g.voff[q], v1 = g.voff[q + 1];
     int p = a.p ? a.p[q] : P;
-    bool ok = a.queue[1] == 0 && o0 >= 0 && o1 >= o0 && o1 <= a.total_rows && p >= 1 && p <= P &&
-              v0 >= 0 && v1 >= v0 && v1 <= g.total_vrows;
-    int n = ok ? (int)(o1 - o0) : 0;
+    bool ok = a.queue[1] == 0 && problem_rows(a, q, o0, nn) && p >= 1 && p <= P && v0 >= 0 &&
+              v1 >= v0 && v1 <= g.total_vrows;
+    int n = ok ? (int)nn : 0;
     int nv = ok ? (int)(v1 - v0) : 0;
     int64_t f = (int64_t)q * a.L + g.pos;
     const float* b = g.b_out + f * P;

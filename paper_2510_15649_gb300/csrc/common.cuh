@@ -43,6 +43,7 @@ struct FitArgs {
   const int32_t* row_idx;
   const int64_t* offsets;
   const int32_t* p;
+  const int32_t* n_rows;  // optional: problem q uses the first n_rows[q] slots of its range
   const float* lambdas;
   const float* b_init;
   float* b_out;
@@ -126,14 +127,28 @@ __device__ __forceinline__ float warp_min(float v) {
 }
 __device__ __forceinline__ float fsign(float v) { return (float)((v > 0.f) - (v < 0.f)); }
 
+// Rows of problem q: slots offsets[q] .. offsets[q] + n - 1 with
+// n = offsets[q+1] - offsets[q], or n_rows[q] (<= that range) when given.
+// Returns false on inconsistent offsets / counts.
+__device__ inline bool problem_rows(const FitArgs& a, int q, int64_t& off0, int64_t& n) {
+  off0 = a.offsets[q];
+  const int64_t off1 = a.offsets[q + 1];
+  if (off0 < 0 || off1 < off0 || off1 > a.total_rows) return false;
+  n = off1 - off0;
+  if (a.n_rows) {
+    const int64_t m = a.n_rows[q];
+    if (m < 0 || m > n) return false;
+    n = m;
+  }
+  return true;
+}
+
 // Validate problem q; on success fill off0, n, p.  Returns false on bad input.
 __device__ inline bool problem_ok(const FitArgs& a, int q, int64_t& off0, int& n, int& p,
                                   int n_cap) {
   if (a.queue[1] != 0) return false;  // offsets failed the monotonicity check
-  off0 = a.offsets[q];
-  int64_t off1 = a.offsets[q + 1];
-  if (off0 < 0 || off1 < off0 || off1 > a.total_rows) return false;
-  int64_t nn = off1 - off0;
+  int64_t nn = 0;
+  if (!problem_rows(a, q, off0, nn)) return false;
   if (nn > (int64_t)a.n_max || nn > (int64_t)n_cap) return false;
   n = (int)nn;
   p = a.p ? a.p[q] : a.P;

@@ -452,14 +452,13 @@ __global__ void __launch_bounds__(128) fit_thread_kernel(FitArgs args) {
   TFit t;
   t.a = &args;
   t.q = q;
-  int64_t o0 = args.offsets[q], o1 = args.offsets[q + 1];
+  int64_t o0 = 0, nn = 0;
   int P = args.P;
-  bool ok = args.queue[1] == 0 && o0 >= 0 && o1 >= o0 && o1 <= args.total_rows &&
-            (o1 - o0) <= (int64_t)args.n_max;
+  bool ok = args.queue[1] == 0 && problem_rows(args, q, o0, nn) && nn <= (int64_t)args.n_max;
   int p = args.p ? args.p[q] : P;
   ok = ok && p >= 1 && p <= P;
   t.off0 = o0;
-  t.n = ok ? (int)(o1 - o0) : 0;
+  t.n = ok ? (int)nn : 0;
   t.p = p;
   if (ok) {
     // validate and gather this problem's rows column-major into its own

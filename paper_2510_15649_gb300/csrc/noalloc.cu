@@ -14,8 +14,8 @@ namespace ll {
 cudaError_t launch_fit_block(const FitArgs& a, cudaStream_t st, int num_sms, int G);
 cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t total_rows, int* ctrl,
                                     cudaStream_t st);
-cudaError_t launch_order(const int64_t* offsets, const int32_t* p, int P, int B, int* order,
-                         cudaStream_t st);
+cudaError_t launch_order(const int64_t* offsets, const int32_t* nr, const int32_t* p, int P, int B,
+                         int* order, cudaStream_t st);
 int fit_block_group(int n_max);
 int fit_block_max_rows(int G, int P);
 }  // namespace ll
@@ -73,7 +73,7 @@ extern "C" int ladlasso_fit_batched_noalloc(const float* X, const float* y, cons
   ladlasso_default_opts(&dflt);
   const ladlasso_opts* o = d->opts ? d->opts : &dflt;
   FitArgs a = {};
-  a.X = X; a.y = y; a.row_idx = row_idx; a.offsets = offsets; a.p = d->p;
+  a.X = X; a.y = y; a.row_idx = row_idx; a.offsets = offsets; a.p = d->p; a.n_rows = d->n_rows;
   a.lambdas = lambdas; a.b_init = d->b_init;
   a.b_out = b_out; a.obj_out = obj_out;
   a.status = d->fit_status; a.basis_out = d->basis_out; a.counters = d->counters;
@@ -102,6 +102,6 @@ extern "C" int ladlasso_fit_batched_noalloc(const float* X, const float* y, cons
   if (cudaMemsetAsync(a.queue, 0, 256, st) != cudaSuccess) return LADLASSO_ERR_CUDA;
   if (launch_validate_offsets(offsets, a.B, a.total_rows, a.queue, st) != cudaSuccess)
     return LADLASSO_ERR_CUDA;
-  if (launch_order(offsets, a.p, a.P, a.B, a.order, st) != cudaSuccess) return LADLASSO_ERR_CUDA;
+  if (launch_order(offsets, a.n_rows, a.p, a.P, a.B, a.order, st) != cudaSuccess) return LADLASSO_ERR_CUDA;
   return launch_fit_block(a, st, sms, G) == cudaSuccess ? LADLASSO_OK : LADLASSO_ERR_CUDA;
 }

@@ -37,7 +37,7 @@ class Opts(C.Structure):
 class Dims(C.Structure):
     _fields_ = [("B", C.c_int32), ("P_cols", C.c_int32), ("L", C.c_int32), ("n_max", C.c_int32),
                 ("ldX", C.c_int64), ("rows_X", C.c_int64), ("total_rows", C.c_int64),
-                ("p", C.c_void_p), ("b_init", C.c_void_p), ("fit_status", C.c_void_p),
+                ("p", C.c_void_p), ("n_rows", C.c_void_p), ("b_init", C.c_void_p), ("fit_status", C.c_void_p),
                 ("basis_out", C.c_void_p), ("counters", C.c_void_p), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("opts", C.c_void_p)]
 
@@ -115,6 +115,7 @@ class Problems:
     p: torch.Tensor | None = None
     P: int = 0
     n_max: int = 0
+    n_rows: torch.Tensor | None = None
 
     @staticmethod
     def from_numpy(batch: dict, device="cuda") -> "Problems":
@@ -143,6 +144,7 @@ class Problems:
         d.rows_X = int(self.X.shape[0])
         d.total_rows = int(self.y.numel())
         d.p = None if self.p is None else self.p.data_ptr()
+        d.n_rows = None if self.n_rows is None else self.n_rows.data_ptr()
         d.b_init = None if b_init is None else b_init.data_ptr()
         d.fit_status = None if status is None else status.data_ptr()
         d.basis_out = None if basis is None else basis.data_ptr()

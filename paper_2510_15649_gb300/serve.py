@@ -1,0 +1,197 @@
+"""Continuous-batching server for LAD-LASSO fits on one GPU.
+
+Requests (one fit each: X [n, p], y [n]) arrive over time.  The server keeps
+a device pool of S fixed-capacity slots (cap rows x P columns each) and runs
+the request loop on the host:
+
+  admit     arrivals whose time has come take a free slot while the device
+            memory they need (n * p floats) fits the pool's budget; their X
+            and y are copied into the slot (one async copy each), their
+            lambda_max and lambda path computed on the device, b zeroed
+  step      one launch of ladlasso_fit_batched over all S slots with L = 1:
+            every active request advances one position of its lambda path,
+            warm-started from its previous b (kept on the device, in place);
+            idle slots are passed with lambda = NaN and 0 rows
+  retire    requests whose path is done copy b and F to the host and free
+            their slot; latency = arrival -> result on the host
+
+Requests that arrive while others are on the GPU join at the next step, so
+work from different requests overlaps inside every launch.  A request's
+results equal those of fitting it alone along the same path (same kernel,
+same per-fit arithmetic).  All arithmetic runs in the CUDA library; this
+module only moves data and keeps the schedule.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import ladlasso as ll
+
+
+@dataclass
+class Result:
+    rid: int
+    b: np.ndarray          # [L, p]
+    obj: np.ndarray        # [L]
+    status: np.ndarray     # [L]
+    lambdas: np.ndarray    # [L]
+    t_arrival: float
+    t_done: float
+
+
+@dataclass
+class ServeStats:
+    completed: int = 0
+    fits: int = 0
+    steps: int = 0
+    wall: float = 0.0
+    latencies: list = field(default_factory=list)
+    max_active: int = 0
+    queued_max: int = 0
+
+    def summary(self) -> dict:
+        lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+        return dict(requests=self.completed, fits=self.fits, steps=self.steps,
+                    seconds=self.wall, fits_per_s=self.fits / max(self.wall, 1e-9),
+                    p50_ms=1e3 * float(np.percentile(lat, 50)),
+                    p99_ms=1e3 * float(np.percentile(lat, 99)),
+                    max_active=self.max_active, max_queued=self.queued_max)
+
+
+class Server:
+    """Slot pool + request loop.  `budget_floats` bounds the total n * p of
+    the active requests (device-memory admission)."""
+
+    def __init__(self, slots: int = 1024, cap: int = 5000, P: int = 64, L: int = 8,
+                 ratio: float = 1e-3, budget_floats: int | None = None, device="cuda",
+                 opts: ll.Opts | None = None):
+        self.S, self.cap, self.P, self.L, self.ratio = slots, cap, P, L, ratio
+        self.dev = torch.device(device)
+        self.opts = opts
+        self.budget = budget_floats if budget_floats is not None else slots * cap * P
+        S, dev = slots, self.dev
+        self.X = torch.zeros((S * cap, P), dtype=torch.float32, device=dev)
+        self.y = torch.zeros(S * cap, dtype=torch.float32, device=dev)
+        self.offsets = torch.arange(S + 1, dtype=torch.int64, device=dev) * cap
+        self.n_rows = torch.zeros(S, dtype=torch.int32, device=dev)
+        self.p = torch.ones(S, dtype=torch.int32, device=dev)
+        self.b = torch.zeros((S, 1, P), dtype=torch.float32, device=dev)
+        self.obj = torch.zeros((S, 1), dtype=torch.float32, device=dev)
+        self.status = torch.zeros((S, 1), dtype=torch.int32, device=dev)
+        self.lam_step = torch.full((S, 1), float("nan"), dtype=torch.float32, device=dev)
+        self.pr = ll.Problems(X=self.X, y=self.y, offsets=self.offsets, p=self.p, P=P,
+                              n_max=cap, n_rows=self.n_rows)
+        self.ws = ll.workspace(self.pr, 1)
+        # host mirrors
+        self.h_n = np.zeros(S, np.int32)
+        self.h_p = np.ones(S, np.int32)
+        self.h_pos = np.zeros(S, np.int32)
+        self.h_rid = np.full(S, -1, np.int64)
+        self.h_lam = np.zeros((S, L), np.float32)
+        self.h_b = np.zeros((S, L, P), np.float32)
+        self.h_obj = np.zeros((S, L), np.float32)
+        self.h_st = np.zeros((S, L), np.int32)
+        self.used = 0
+        self.free = list(range(S - 1, -1, -1))
+
+    # ---------------------------------------------------------------- admit
+    def _admit(self, reqs, rids):
+        slots = []
+        for r, rid in zip(reqs, rids):
+            s = self.free.pop()
+            n, p = r["X"].shape
+            self.X[s * self.cap:s * self.cap + n, :p].copy_(torch.from_numpy(r["X"]))
+            self.y[s * self.cap:s * self.cap + n].copy_(torch.from_numpy(r["y"]))
+            self.h_n[s], self.h_p[s], self.h_pos[s], self.h_rid[s] = n, p, 0, rid
+            self.used += n * p
+            slots.append(s)
+        self.n_rows.copy_(torch.from_numpy(self.h_n), non_blocking=True)
+        self.p.copy_(torch.from_numpy(self.h_p), non_blocking=True)
+        # lambda_max and the path of the new requests, on the device
+        ss = np.array(sorted(slots), np.int64)
+        offs = torch.from_numpy(np.append(ss * self.cap, ss[-1] * self.cap + self.cap)).to(self.dev)
+        sub = ll.Problems(X=self.X, y=self.y, offsets=offs,
+                          p=torch.from_numpy(self.h_p[ss]).to(self.dev), P=self.P,
+                          n_max=self.cap,
+                          n_rows=torch.from_numpy(self.h_n[ss]).to(self.dev))
+        lmax = ll.lambda_max(sub, self.ws)
+        lam = ll.lambda_path(lmax, self.L, self.ratio)
+        self.h_lam[ss] = lam.cpu().numpy()
+        self.b[torch.from_numpy(ss).to(self.dev)] = 0.0
+        return slots
+
+    # ---------------------------------------------------------------- run
+    def run(self, trace: list, time_scale: float = 1.0) -> tuple:
+        """Serve `trace` (list of dicts with t, X, y), arrivals replayed in
+        real time scaled by time_scale.  Returns (results, ServeStats)."""
+        st = ServeStats()
+        results = []
+        t0 = time.perf_counter()
+        arrive = {i: t0 + trace[i]["t"] * time_scale for i in range(len(trace))}
+        queue = []
+        nxt = 0
+        while nxt < len(trace) or queue or np.any(self.h_rid >= 0):
+            now = time.perf_counter()
+            while nxt < len(trace) and arrive[nxt] <= now:
+                queue.append(nxt)
+                nxt += 1
+            st.queued_max = max(st.queued_max, len(queue))
+            adm, adm_ids, extra = [], [], 0
+            while queue and len(adm) < len(self.free):
+                i = queue[0]
+                n, p = trace[i]["X"].shape
+                if n > self.cap or p > self.P:
+                    raise ValueError(f"request {i} ({n}x{p}) exceeds the slot capacity")
+                if self.used + extra + n * p > self.budget:
+                    break  # device-memory admission: wait for requests to retire
+                queue.pop(0)
+                adm.append(trace[i])
+                adm_ids.append(i)
+                extra += n * p
+            if adm:
+                self._admit(adm, adm_ids)
+            active = np.nonzero(self.h_rid >= 0)[0]
+            if len(active) == 0:
+                if nxt < len(trace):  # idle until the next arrival
+                    time.sleep(max(0.0, min(arrive[nxt] - time.perf_counter(), 1e-3)))
+                continue
+            st.max_active = max(st.max_active, len(active))
+            lam = np.full(self.S, np.nan, np.float32)
+            lam[active] = self.h_lam[active, self.h_pos[active]]
+            self.lam_step.copy_(torch.from_numpy(lam).reshape(self.S, 1), non_blocking=True)
+            ll.fit(self.pr, self.lam_step, b_init=self.b, ws=self.ws, opts=self.opts,
+                   out=dict(b=self.b, obj=self.obj, status=self.status))
+            st.steps += 1
+            # every active request advanced one position; copy this step's results
+            bh = self.b.cpu().numpy()[:, 0]
+            oh = self.obj.cpu().numpy()[:, 0]
+            sh = self.status.cpu().numpy()[:, 0]
+            pos = self.h_pos[active]
+            self.h_b[active, pos] = bh[active]
+            self.h_obj[active, pos] = oh[active]
+            self.h_st[active, pos] = sh[active]
+            self.h_pos[active] += 1
+            st.fits += len(active)
+            done = active[self.h_pos[active] >= self.L]
+            tnow = time.perf_counter()
+            for s in done:
+                rid = int(self.h_rid[s])
+                p = int(self.h_p[s])
+                results.append(Result(rid=rid, b=self.h_b[s, :, :p].copy(),
+                                      obj=self.h_obj[s].copy(), status=self.h_st[s].copy(),
+                                      lambdas=self.h_lam[s].copy(), t_arrival=arrive[rid],
+                                      t_done=tnow))
+                st.latencies.append(tnow - arrive[rid])
+                self.used -= int(self.h_n[s]) * p
+                self.h_rid[s] = -1
+                self.h_n[s] = 0
+                self.free.append(int(s))
+                st.completed += 1
+            if len(done):
+                self.n_rows.copy_(torch.from_numpy(self.h_n), non_blocking=True)
+        st.wall = time.perf_counter() - t0
+        return results, st
