@@ -216,10 +216,8 @@ def main():
             times.append(e0.elapsed_time(e1) / 1e3)
     t_step = statistics.median(times)
     log(f"timed steps {times}")
-    if dist is not None:
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    from paper_2510_15649_gb300.dist import max_over_ranks
+    t_step = max_over_ranks(t_step, dist, dev)  # the slowest rank sets the job time
     st = out["status"].cpu().numpy()
     cnt = out["counters"].cpu().numpy()
     certified = int(np.sum((st & 3) == 0))
