@@ -85,6 +85,10 @@ typedef struct ladlasso_opts {
   int32_t max_pivots;     /* polish step cap; 0 = 4*p + 64                    (0) */
   float tol_opt;          /* multiplier tolerance                             (2e-5) */
   float lambda_min_floor; /* lambda := max(lambda, floor), Section 3.5        (0) */
+  int32_t chop_sections;  /* 3: ternary chop (Section 3.4); 4: the "quadrature"
+                             search read as four sections probed at the three
+                             inner points, keeping the two around the lowest
+                             (Sections 1 and 5 name it, undefined)        (3) */
 } ladlasso_opts;
 
 /* Fills `o` with the defaults above.  Never fails. */
@@ -114,7 +118,17 @@ void ladlasso_default_opts(ladlasso_opts* o);
  *            are counted by the batched kernel only, else 0)
  * workspace  device scratch of at least ladlasso_workspace_size(...) bytes,
  *            256-byte aligned; contents need not be initialised
- * opts     host pointer or NULL for defaults */
+ * opts     host pointer or NULL for defaults
+ * group_threads   launch shape of ladlasso_fit_batched (and _noalloc):
+ *            0 = automatic (one warp per fit up to 8192 rows, else one
+ *            512-thread block per fit), 32 = one warp per fit, 512 = one
+ *            block per fit; any other value is LADLASSO_ERR_INVALID.  The
+ *            two shapes sum in different orders: results agree within the
+ *            float32 tolerance, not bit for bit
+ * fits_per_block  one-warp shape: at most this many fits per thread block
+ *            (0 = as many as shared memory holds, at most 16); results do
+ *            not depend on it.  Both are chosen by the autotuner of the
+ *            Python binding; zero-initialise them otherwise */
 typedef struct ladlasso_dims {
   int32_t B, P_cols, L;
   int32_t n_max;
@@ -128,6 +142,8 @@ typedef struct ladlasso_dims {
   void* workspace;
   size_t workspace_bytes;
   const ladlasso_opts* opts;
+  int32_t group_threads;
+  int32_t fits_per_block;
 } ladlasso_dims;
 
 /* Bytes of device workspace any entry point below needs for a problem set
@@ -150,16 +166,43 @@ int ladlasso_lambda_path(const float* lmax, int32_t B, int32_t L, float ratio,
 
 /* Fit every problem along its lambda path (descending order expected;
  * each path position warm-starts from the previous solution).
- * One warp holds one fit (several independent fits per thread block; one
- * block per fit beyond 8192 rows): residual, selection buffer and the p x p
- * algebra in shared memory, the gathered design in the workspace; warps take
- * problems from a device work queue.
+ * One warp holds one fit (several independent fits per thread block) while
+ * n_max <= 8192: residual, the current and next column, selection buffer
+ * and the p x p algebra in shared memory.  Beyond 8192 rows one 512-thread
+ * block holds one fit: residual, selection buffers and the p x p algebra in
+ * shared memory, the columns streamed from the gathered design in the
+ * workspace.  Warps (blocks) take problems from a device work queue, longest
+ * first.  LADLASSO_ERR_NOMEM when n_max exceeds what one block's shared
+ * memory holds (about 34000 rows at P_cols = 128).
  *   lambdas [B*L], b_out [B*L*P_cols], obj_out [B*L] device.
  * obj_out holds F at the returned b. */
 int ladlasso_fit_batched(const float* X, const float* y, const int32_t* row_idx,
                          const int64_t* offsets, const float* lambdas,
                          float* b_out, float* obj_out, const ladlasso_dims* dims,
                          ladlasso_stream_t stream);
+
+/* LAD loss of every path position on a set of held-out rows:
+ *   loss_out[q*L + l] = sum over rows v of problem q of |y_v - x_v . b_{q,l}|
+ * with b_{q,l} = b_out[(q*L + l)*P_cols ..] (the first p_q entries), the
+ * validation loss by which a lambda is chosen (Sections 2 and 6 fit the
+ * regularisation on held-out data; the paper gives no formula).  X, y,
+ * row_idx, offsets and dims describe the held-out rows like a problem set
+ * (dims: B, P_cols, L, ldX, rows_X, total_rows, p; other fields unused; no
+ * workspace).  A problem with out-of-range rows, bad offsets or a
+ * non-finite residual gets NaN.  loss_out [B*L] device. */
+int ladlasso_path_loss(const float* X, const float* y, const int32_t* row_idx,
+                       const int64_t* offsets, const ladlasso_dims* dims, const float* b_out,
+                       float* loss_out, ladlasso_stream_t stream);
+
+/* The launch shape ladlasso_fit_batched would use for `dims` (only
+ * B-independent fields are read: P_cols, n_max, group_threads,
+ * fits_per_block): threads per fit (32 or 512), fits per thread block, and
+ * the largest n_max that shape supports at this P_cols.  No launch, no
+ * device access.  Returns LADLASSO_ERR_NOMEM when n_max exceeds max_rows,
+ * LADLASSO_ERR_INVALID for invalid fields.  The paper has no counterpart:
+ * it serves the autotuner. */
+int ladlasso_launch_shape(const ladlasso_dims* dims, int32_t* group_threads,
+                          int32_t* fits_per_block, int32_t* max_rows);
 
 /* The same method and options with one GPU thread per fit -- the layout the
  * paper proposes for a browser GPU (Sections 1 and 5) -- kept as the plain
@@ -209,7 +252,7 @@ int ladlasso_fit_backward(const float* X, const float* y, const int32_t* row_idx
  * scratch is one fixed 32 MiB device array inside the library, which every
  * GPU that loads the library holds until the process exits.  A problem set
  * whose scratch, 256 + round_up(4*B, 256) + (total_rows + 4*B) *
- * round_up(P_cols, 4) * 4 bytes, exceeds 32 MiB is rejected with
+ * (round_up(P_cols, 4) + 4) * 4 bytes, exceeds 32 MiB is rejected with
  * LADLASSO_ERR_NOMEM before any launch.
  * The first call on a device looks up the array's device address (with
  * that device current); make that first call before any stream capture.

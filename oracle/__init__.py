@@ -42,7 +42,8 @@ class Opts(C.Structure):
                 ("chop_tol", C.c_double), ("chop_max_probes", C.c_int),
                 ("chop_max_extend", C.c_int), ("probe_max_sweeps", C.c_int),
                 ("polish", C.c_int), ("max_pivots", C.c_int),
-                ("tol_opt", C.c_double), ("lambda_min_floor", C.c_double)]
+                ("tol_opt", C.c_double), ("lambda_min_floor", C.c_double),
+                ("chop_sections", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -76,6 +76,7 @@ typedef struct {
   int max_pivots;        /* polish step cap */
   double tol_opt;        /* multiplier tolerance, times max(1,lambda) */
   double lambda_min_floor; /* Section 3.5: a small minimum lambda disambiguates flat LAD minima */
+  int chop_sections;     /* 3: ternary chop; 4: the "quadrature" reading (3 interior probes) */
 } orc_opts;
 
 typedef struct {
@@ -96,6 +97,7 @@ void orc_default_opts(orc_opts* o) {
   o->chop_tol = 1e-3;
   o->chop_max_probes = 12;
   o->chop_max_extend = 20;
+  o->chop_sections = 3;
   o->probe_max_sweeps = 4;
   o->polish = 1;
   o->max_pivots = 2000;
@@ -358,13 +360,28 @@ int orc_chop(int n, int p, const double* X, const double* y, double* b,
   st->extends += ext;
   double lo = a, hi = e;
   int probes = 0;
-  while (hi - lo > o->chop_tol * scale && probes + 2 <= o->chop_max_probes) {
-    double m1 = lo + (hi - lo) / 3.0, m2 = hi - (hi - lo) / 3.0;
-    double g1 = probe(&c, m1), g2 = probe(&c, m2);
-    probes += 2;
-    if (g1 < g2) hi = m2;
-    else if (g1 > g2) lo = m1;
-    else { lo = m1; hi = m2; }
+  if (o->chop_sections == 4) {
+    /* four equal sections, probes at the three inner points; for a convex
+     * g the minimum lies within one section of the lowest probe, so keep
+     * the two sections around it (the leftmost lowest on ties) */
+    while (hi - lo > o->chop_tol * scale && probes + 3 <= o->chop_max_probes) {
+      double h = (hi - lo) / 4.0;
+      double t1 = lo + h, t2 = lo + 2.0 * h, t3 = hi - h;
+      double g1 = probe(&c, t1), g2 = probe(&c, t2), g3 = probe(&c, t3);
+      probes += 3;
+      if (g1 <= g2 && g1 <= g3) hi = t2;
+      else if (g2 <= g3) { lo = t1; hi = t3; }
+      else lo = t2;
+    }
+  } else {
+    while (hi - lo > o->chop_tol * scale && probes + 2 <= o->chop_max_probes) {
+      double m1 = lo + (hi - lo) / 3.0, m2 = hi - (hi - lo) / 3.0;
+      double g1 = probe(&c, m1), g2 = probe(&c, m2);
+      probes += 2;
+      if (g1 < g2) hi = m2;
+      else if (g1 > g2) lo = m1;
+      else { lo = m1; hi = m2; }
+    }
   }
   int improved = c.best_f < f0;
   if (improved) {

@@ -5,7 +5,10 @@
 #include "common.cuh"
 
 namespace ll {
-cudaError_t launch_fit_block(const FitArgs& a, cudaStream_t st, int num_sms, int G);
+cudaError_t launch_fit_block(const FitArgs& a, cudaStream_t st, int num_sms, int G,
+                             int fits_per_block);
+int launch_group(const ladlasso_dims* d);
+int fit_block_fits_per_block(int G, int P, int n_max, int fits_per_block);
 int fit_block_group(int n_max);
 int fit_block_max_rows(int G, int P);
 cudaError_t launch_fit_thread(const FitArgs& a, cudaStream_t st, int num_sms);
@@ -16,6 +19,10 @@ cudaError_t launch_order(const int64_t* offsets, const int32_t* nr, const int32_
                          int* order, cudaStream_t st);
 cudaError_t launch_lambda_path(const float* lmax, int B, int L, float ratio, float* lam,
                                cudaStream_t st);
+cudaError_t launch_path_loss(const float* X, int64_t ldX, int64_t rows_X, const float* y,
+                             const int32_t* row_idx, const int64_t* offsets, int64_t total_rows,
+                             const int32_t* p, int P, const float* b, int B, int L, float* loss,
+                             cudaStream_t st, int num_sms);
 cudaError_t launch_backward(const FitArgs& a, int pos, const float* b_out, const int32_t* basis,
                             const float* Xv, int64_t ldXv, const float* yv, const int32_t* vrow,
                             const int64_t* voff, int64_t total_vrows, const float* gup,
@@ -49,7 +56,7 @@ bool ws_layout(int32_t B, int32_t P, int64_t total_rows, WsLayout* w) {
   size_t rows = (size_t)total_rows + 4 * (size_t)B;
   w->ctrl = 0;
   w->xg = ll::ws_xg_offset(B);
-  size_t xg_bytes = align256(rows * P4 * sizeof(float));
+  size_t xg_bytes = align256(rows * (size_t)ll::xg_slots((int)P4) * sizeof(float));
   w->scratch = w->xg + xg_bytes;
   // thread-per-fit scratch: per slot (key, weight, id, residual) for
   // total_rows + B*(P+1) slots, plus per problem a P x P matrix and 16 P-vectors
@@ -76,13 +83,15 @@ ll::Opts to_opts(const ladlasso_opts* o) {
   r.max_pivots = o->max_pivots;
   r.tol_opt = o->tol_opt;
   r.lambda_min_floor = o->lambda_min_floor;
+  r.chop_sections = o->chop_sections;
   return r;
 }
 
 bool opts_ok(const ll::Opts& o) {
   return o.tol_move >= 0.f && o.max_sweeps >= 1 && o.chop_bracket > 0.f && o.chop_tol >= 0.f &&
          o.chop_max_probes >= 0 && o.chop_max_extend >= 0 && o.probe_max_sweeps >= 1 &&
-         o.max_pivots >= 0 && o.tol_opt >= 0.f && o.lambda_min_floor >= 0.f;
+         o.max_pivots >= 0 && o.tol_opt >= 0.f && o.lambda_min_floor >= 0.f &&
+         (o.chop_sections == 3 || o.chop_sections == 4);
 }
 
 // Common checks and FitArgs set-up.  Returns LADLASSO_OK or an error.
@@ -155,6 +164,7 @@ void ladlasso_default_opts(ladlasso_opts* o) {
   o->max_pivots = 0;
   o->tol_opt = 2e-5f;
   o->lambda_min_floor = 0.f;
+  o->chop_sections = 3;
 }
 
 size_t ladlasso_workspace_size(int32_t B, int32_t P_cols, int64_t total_rows, int32_t L) {
@@ -192,7 +202,8 @@ static int fit_common(const float* X, const float* y, const int32_t* row_idx,
   int rc = prepare(X, y, row_idx, offsets, dims, &a);
   if (rc != LADLASSO_OK) return rc;
   if (!lambdas || !b_out || !obj_out) return LADLASSO_ERR_INVALID;
-  const int G = ll::fit_block_group(dims->n_max);
+  const int G = ll::launch_group(dims);
+  if (G == 0 || dims->fits_per_block < 0) return LADLASSO_ERR_INVALID;
   if (!per_thread && dims->n_max > ll::fit_block_max_rows(G, dims->P_cols)) return LADLASSO_ERR_NOMEM;
   a.lambdas = lambdas;
   a.b_out = b_out;
@@ -206,7 +217,7 @@ static int fit_common(const float* X, const float* y, const int32_t* row_idx,
   if (!per_thread && ll::launch_order(a.offsets, a.n_rows, a.p, a.P, a.B, a.order, st) != cudaSuccess)
     return LADLASSO_ERR_CUDA;
   cudaError_t e = per_thread ? ll::launch_fit_thread(a, st, sms)
-                             : ll::launch_fit_block(a, st, sms, G);
+                             : ll::launch_fit_block(a, st, sms, G, dims->fits_per_block);
   return cuda_status(e);
 }
 
@@ -214,6 +225,36 @@ int ladlasso_fit_batched(const float* X, const float* y, const int32_t* row_idx,
                          const int64_t* offsets, const float* lambdas, float* b_out,
                          float* obj_out, const ladlasso_dims* dims, ladlasso_stream_t stream) {
   return fit_common(X, y, row_idx, offsets, lambdas, b_out, obj_out, dims, stream, false);
+}
+
+int ladlasso_path_loss(const float* X, const float* y, const int32_t* row_idx,
+                       const int64_t* offsets, const ladlasso_dims* d, const float* b_out,
+                       float* loss_out, ladlasso_stream_t stream) {
+  if (!d || !offsets || !b_out || !loss_out) return LADLASSO_ERR_INVALID;
+  if (d->B < 0 || d->L < 1 || d->P_cols < 1 || d->P_cols > ll::kMaxP || d->ldX < d->P_cols ||
+      d->rows_X < 0 || d->total_rows < 0)
+    return LADLASSO_ERR_INVALID;
+  if (d->total_rows > 0 && (!y || (!X && d->rows_X > 0))) return LADLASSO_ERR_INVALID;
+  if (!row_idx && d->total_rows > d->rows_X) return LADLASSO_ERR_INVALID;
+  if (d->B == 0) return LADLASSO_OK;
+  const int sms = num_sms();
+  if (sms <= 0) return LADLASSO_ERR_CUDA;
+  return cuda_status(ll::launch_path_loss(X, d->ldX, d->rows_X, y, row_idx, offsets,
+                                          d->total_rows, d->p, d->P_cols, b_out, d->B, d->L,
+                                          loss_out, (cudaStream_t)stream, sms));
+}
+
+int ladlasso_launch_shape(const ladlasso_dims* dims, int32_t* group_threads,
+                          int32_t* fits_per_block, int32_t* max_rows) {
+  if (!dims || !group_threads || !fits_per_block || !max_rows) return LADLASSO_ERR_INVALID;
+  if (dims->P_cols < 1 || dims->P_cols > ll::kMaxP || dims->n_max < 0 || dims->fits_per_block < 0)
+    return LADLASSO_ERR_INVALID;
+  const int G = ll::launch_group(dims);
+  if (G == 0) return LADLASSO_ERR_INVALID;
+  *group_threads = G;
+  *fits_per_block = ll::fit_block_fits_per_block(G, dims->P_cols, dims->n_max, dims->fits_per_block);
+  *max_rows = ll::fit_block_max_rows(G, dims->P_cols);
+  return dims->n_max > *max_rows ? LADLASSO_ERR_NOMEM : LADLASSO_OK;
 }
 
 int ladlasso_fit_batched_thread(const float* X, const float* y, const int32_t* row_idx,

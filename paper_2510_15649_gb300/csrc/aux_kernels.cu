@@ -102,7 +102,66 @@ __global__ void lambda_path_kernel(const float* lmax, int B, int L, float ratio,
   }
 }
 
+// LAD loss of every path position on a row set: one block per problem
+// (grid-stride), threads stride over the rows, fixed-order reductions.
+// A problem with bad rows, offsets or p gets NaN.
+__global__ void path_loss_kernel(const float* X, int64_t ldX, int64_t rows_X, const float* y,
+                                 const int32_t* row_idx, const int64_t* offsets,
+                                 int64_t total_rows, const int32_t* pv, int P, const float* b,
+                                 int B, int L, float* loss) {
+  __shared__ float bs[kMaxP];
+  __shared__ float red[32];
+  __shared__ int bad_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x / 32;
+  for (int q = blockIdx.x; q < B; q += gridDim.x) {
+    const int64_t o0 = offsets[q], o1 = offsets[q + 1];
+    const int p = pv ? pv[q] : P;
+    const bool ok = o0 >= 0 && o1 >= o0 && o1 <= total_rows && p >= 1 && p <= P;
+    if (tid == 0) bad_s = ok ? 0 : 1;
+    __syncthreads();
+    for (int l = 0; l < L; ++l) {
+      const float* bq = b + ((int64_t)q * L + l) * P;
+      for (int c = tid; c < P; c += blockDim.x) bs[c] = bq[c];
+      __syncthreads();
+      float acc = 0.f;
+      int bad = 0;
+      if (ok) {
+        for (int64_t i = o0 + tid; i < o1; i += blockDim.x) {
+          const int64_t row = row_idx ? (int64_t)row_idx[i] : i;
+          if (row < 0 || row >= rows_X) { bad = 1; continue; }
+          const float* x = X + row * ldX;
+          float r = y[i];
+          for (int c = 0; c < p; ++c) r -= x[c] * bs[c];
+          if (!isfinite(r)) bad = 1;
+          acc += fabsf(r);
+        }
+      }
+      if (bad) atomicOr(&bad_s, 1);
+      acc = warp_sum(acc);
+      if (lane == 0) red[warp] = acc;
+      __syncthreads();
+      if (tid == 0) {
+        float t = 0.f;
+        for (int w = 0; w < nw; ++w) t += red[w];
+        loss[(int64_t)q * L + l] = bad_s ? NAN : t;
+      }
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_path_loss(const float* X, int64_t ldX, int64_t rows_X, const float* y,
+                             const int32_t* row_idx, const int64_t* offsets, int64_t total_rows,
+                             const int32_t* p, int P, const float* b, int B, int L, float* loss,
+                             cudaStream_t st, int num_sms) {
+  if (B <= 0) return cudaSuccess;
+  int grid = B < num_sms * 8 ? B : num_sms * 8;
+  path_loss_kernel<<<grid, 256, 0, st>>>(X, ldX, rows_X, y, row_idx, offsets, total_rows, p, P,
+                                         b, B, L, loss);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t total_rows, int* ctrl,
                                     cudaStream_t st) {

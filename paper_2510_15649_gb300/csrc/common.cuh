@@ -34,6 +34,7 @@ struct Opts {
   int max_pivots;
   float tol_opt;
   float lambda_min_floor;
+  int chop_sections;  // 3 ternary, 4 four-section ("quadrature")
 };
 
 // Everything a fit kernel needs; passed by value.
@@ -64,12 +65,15 @@ struct FitArgs {
 // Workspace layout (bytes, 256-aligned sections):
 //   [0, 256)            control words (work counters)
 //   order               B ints: problems in decreasing estimated cost
-//   Xg                  (total_rows + 4 B) * P4 floats: problem q's column j
-//                       starts at xg_base(q) + j * ld(n_q), ld = round_up(n,4)
+//   Xg                  (total_rows + 4 B) * (P4 + 4) floats: problem q's
+//                       column j starts at xg_base(q) + j * ld(n_q),
+//                       ld = round_up(n, 4); column slot P4 holds the edge
+//                       products x_i . d of the block-per-fit polish
 //   thread scratch      per-slot and per-problem scratch for the
 //                       thread-per-fit kernel
+__host__ __device__ inline int64_t xg_slots(int P4) { return (int64_t)P4 + 4; }
 __host__ __device__ inline int64_t xg_base(int64_t off_q, int q, int P4) {
-  return (off_q + 4 * (int64_t)q) * P4;
+  return (off_q + 4 * (int64_t)q) * xg_slots(P4);
 }
 __host__ __device__ inline int64_t xg_ld(int n) { return ((int64_t)n + 3) & ~(int64_t)3; }
 __host__ __device__ inline size_t ws_order_offset() { return 256; }
@@ -92,6 +96,17 @@ __device__ __forceinline__ void sts_f(uint32_t a, float v) {
 }
 __device__ __forceinline__ void sts_i(uint32_t a, int v) {
   asm volatile("st.shared.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+// Global-window load (data written earlier in the same launch: a plain
+// coherent load, kept in program order with the barriers around it).
+__device__ __forceinline__ float ldg_f(const float* p) {
+  float v;
+  asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(__cvta_generic_to_global(p)));
+  return v;
+}
+// Hint: bring the 128-byte line holding p into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
 }
 // 16-byte global -> shared copy that bypasses registers (completes
 // asynchronously; wait with cp_async_wait_all).

@@ -43,6 +43,8 @@ constexpr int kU = 4;          // elements per thread per compaction chunk
 constexpr int kBufCap = 256;   // selection buffer of the one-warp path
 constexpr int kMaxPasses = 64; // cap on fused passes per 1-D step
 constexpr int kAxis = 0, kEdge = 1;
+constexpr int kSubCap = 128;   // block path: selection sub-buffer per warp
+constexpr int kBlockG = 512;   // block path: threads per fit
 // dynamic shared memory one block may take: 227 KB less the static state
 constexpr size_t kDynSmemLimit = 227 * 1024 - 8 * 1024;
 
@@ -54,25 +56,30 @@ struct St {
   float* Bm;                           // [P*P]
   float* red2;                         // [W*P]
   int* code; int* phan; int* piv; int* perm; int* pcol;  // [P]
+  int* code_prev; int* phan_prev;  // [P] last path position's final basis
+  int* code_alt; int* phan_alt;    // [P] the other polish start
   float* sk; float* sw; int* sid;      // special breakpoints [P+1]
   unsigned* mask;                      // basis-row bitmap [maskw]
   float* redf; int* redi;              // reductions [W*16]
   float* sampk; float* sampw;          // [32]
   int cap, maskw;
+  int* wcnt;         // block path: keys inside the window per warp [W]
+  float* vdg;        // block path: edge products x_i . d (global scratch)
   const FitArgs* a;
   const float* Xq;   // gathered design (column j at Xq + j*ld)
   float* cb[2];      // one warp: double-buffered copy of the current column
   int cur;           // buffer holding the column of the current axis step
   const float* yq;   // targets
   const float* colp; // current column (axis steps)
+  const float* vd;   // one warp, polish: v_i = x_i . d of the edge (a column buffer)
   int n, p, ld, nspec, qcode;
   float lam, bj;
   // broadcast slots
   float lo, hi, acc, wpart, half, zstar, above;
-  int part, m, owner, q, flag, iter, first;
+  int part, m, owner, q, flag, iter, first, has_prev;
   // fused-pass results
   float p_wl, p_wi, p_wt, p_amin;
-  int p_cnt;
+  int p_cnt, p_ovf;
   // per-fit counters
   int passes, selects, sel_fail;
 };
@@ -431,12 +438,16 @@ __device__ __forceinline__ void row_key(const St& s, int i, float& k, float& w) 
     w = fabsf(x);
   } else {
     float v = 0.f;
-    for (int c = 0; c < s.p; ++c) {
-      const float dc = s.dv[c];
-      if (dc != 0.f) v += xval(s, c, i) * dc;  // d is zero on basis coordinates
+    if (s.vd) {
+      v = s.vd[i];  // basis rows other than the released one already hold 0
+    } else {
+      for (int c = 0; c < s.p; ++c) {
+        const float dc = s.dv[c];
+        if (dc != 0.f) v += xval(s, c, i) * dc;  // d is zero on basis coordinates
+      }
+      const bool inb = (s.mask[i >> 5] >> (i & 31)) & 1u;
+      if (inb && i != s.qcode) v = 0.f;
     }
-    const bool inb = (s.mask[i >> 5] >> (i & 31)) & 1u;
-    if (inb && i != s.qcode) v = 0.f;
     k = i == s.qcode ? 0.f : (v != 0.f ? __fdividef(s.rr[i], v) : kInf);
     w = fabsf(v);
   }
@@ -455,7 +466,7 @@ constexpr int kPassU = 8;
 __device__ __forceinline__ void classify_one(float* __restrict__ bk, float* __restrict__ bw,
                                              int* __restrict__ bi, float k, float w, int id,
                                              bool valid, float lo, float hi, float& al, float& ale,
-                                             float& at, float& amin, int& base) {
+                                             float& at, float& amin, int& base, int cap) {
   const int lane = lane_id();
   at += w;
   if (k < lo) al += w;
@@ -464,18 +475,17 @@ __device__ __forceinline__ void classify_one(float* __restrict__ bk, float* __re
   if (k > hi) amin = fminf(amin, k);
   const unsigned msk = __ballot_sync(0xffffffffu, in);
   const int pos = base + __popc(msk & ((1u << lane) - 1u));
-  if (in && pos < kBufCap) { bk[pos] = k; bw[pos] = w; bi[pos] = id; }
+  if (in && pos < cap) { bk[pos] = k; bw[pos] = w; bi[pos] = id; }
   base += __popc(msk);
 }
 
-// Axis-step rows: z = b_j + r_i / x_ij, weight |x_ij|.  Full batches of
-// 32 * kPassU rows run without bounds checks; the compaction code runs only
-// when some lane of the warp holds a key inside the window.
-// Axis-step rows from shared memory (the column buffer and the residual):
-// z = b_j + r_i / x_ij, weight |x_ij|.  Full batches of 32 * kPassU rows run
-// without bounds checks; the compaction code runs only when some lane of
-// the warp holds a key inside the window.
-__device__ __forceinline__ void axis_rows(uint32_t col_s, uint32_t rr_s, float bj, int n,
+// Rows from shared memory (a per-row factor x_i and the residual r_i):
+//   kAxis: x_i = x_ij,     z = b_j + r_i / x_i, weight |x_i|
+//   kEdge: x_i = x_i . d,  t = r_i / x_i (0 for the released row `qc`)
+// Batches of 32 * kPassU rows; the compaction code runs only when some lane
+// of the warp holds a key inside the window.
+template <int MODE>
+__device__ __forceinline__ void smem_rows(uint32_t col_s, uint32_t rr_s, float bj, int qc, int n,
                                           float lo, float hi, uint32_t bk_s, uint32_t bw_s,
                                           uint32_t bi_s, float& al, float& ale, float& at,
                                           float& amin, int& base) {
@@ -495,7 +505,9 @@ __device__ __forceinline__ void axis_rows(uint32_t col_s, uint32_t rr_s, float b
       const int e = i0 + u * 32 + lane;
       const float x = xv[u];  // zero beyond n: no weight, key +inf
       const float w = fabsf(x);
-      const float k = x != 0.f ? bj + __fdividef(rv[u], x) : kInf;
+      float k;
+      if (MODE == kAxis) k = x != 0.f ? bj + __fdividef(rv[u], x) : kInf;
+      else k = e == qc ? 0.f : (x != 0.f ? __fdividef(rv[u], x) : kInf);
       at += w;
       al += k < lo ? w : 0.f;
       ale += k <= hi ? w : 0.f;
@@ -525,14 +537,17 @@ __device__ __noinline__ void fused_pass(St& s, float lo, float hi) {
   float al = 0.f, ale = 0.f, at = 0.f, amin = kInf;
   int base = 0;
   if (MODE == kAxis) {
-    axis_rows(smem_u32(s.colp), smem_u32(s.rr), s.bj, n, lo, hi, smem_u32(bk), smem_u32(bw),
-              smem_u32(bi), al, ale, at, amin, base);
+    smem_rows<kAxis>(smem_u32(s.colp), smem_u32(s.rr), s.bj, 0, n, lo, hi, smem_u32(bk),
+                     smem_u32(bw), smem_u32(bi), al, ale, at, amin, base);
+  } else if (s.vd) {
+    smem_rows<kEdge>(smem_u32(s.vd), smem_u32(s.rr), 0.f, s.qcode, n, lo, hi, smem_u32(bk),
+                     smem_u32(bw), smem_u32(bi), al, ale, at, amin, base);
   } else {
     for (int i0 = 0; i0 < n; i0 += 32) {
       const int e = i0 + lane;
       float k = kInf, w = 0.f;
       if (e < n) row_key<MODE>(s, e, k, w);
-      classify_one(bk, bw, bi, k, w, e, e < n, lo, hi, al, ale, at, amin, base);
+      classify_one(bk, bw, bi, k, w, e, e < n, lo, hi, al, ale, at, amin, base, kBufCap);
     }
   }
   const float* __restrict__ sk = s.sk;
@@ -542,7 +557,7 @@ __device__ __noinline__ void fused_pass(St& s, float lo, float hi) {
     const int e = j0 + lane;
     const bool v = e < nspec;
     classify_one(bk, bw, bi, v ? sk[e] : kInf, v ? sw[e] : 0.f, v ? sid[e] : 0, v, lo, hi, al,
-                 ale, at, amin, base);
+                 ale, at, amin, base, kBufCap);
   }
   al = warp_sum(al);
   ale = warp_sum(ale);
@@ -557,19 +572,10 @@ __device__ __noinline__ void fused_pass(St& s, float lo, float hi) {
 // `frac` of its weight, from 32 sampled keys: strided rows, or strided
 // buffer entries when `nbuf` > 0.  Fewer than 8 samples inside: the whole
 // interval.
-template <int MODE>
-__device__ __noinline__ void region_window(St& s, float rl, float ru, float frac, int nbuf) {
+// (one warp) the window from one sampled key per lane (k, w).
+__device__ __forceinline__ void window_from_samples(St& s, float k, float w, float rl, float ru,
+                                                    float frac) {
   const int lane = lane_id();
-  const int n = s.n;
-  float k = kInf, w = 0.f;
-  if (nbuf > 0) {
-    const int e = (int)(((int64_t)lane * nbuf) / 32);
-    k = s.ck[e];
-    w = s.cw[e];
-  } else if (n > 0) {
-    const int i = n >= 32 ? (int)(((int64_t)lane * n) / 32) : lane;
-    if (i < n) row_key<MODE>(s, i, k, w);
-  }
   const bool ok = k > rl && k < ru && w > 0.f;
   if (!ok) { k = kInf; w = 0.f; }
   const int cnt = __popc(__ballot_sync(0xffffffffu, ok));
@@ -590,6 +596,22 @@ __device__ __noinline__ void region_window(St& s, float rl, float ru, float frac
   __syncwarp();
   if (lane == 0) { s.lo = lo; s.hi = hi; }
   __syncwarp();
+}
+
+template <int MODE>
+__device__ __noinline__ void region_window(St& s, float rl, float ru, float frac, int nbuf) {
+  const int lane = lane_id();
+  const int n = s.n;
+  float k = kInf, w = 0.f;
+  if (nbuf > 0) {
+    const int e = (int)(((int64_t)lane * nbuf) / 32);
+    k = s.ck[e];
+    w = s.cw[e];
+  } else if (n > 0) {
+    const int i = n >= 32 ? (int)(((int64_t)lane * n) / 32) : lane;
+    if (i < n) row_key<MODE>(s, i, k, w);
+  }
+  window_from_samples(s, k, w, rl, ru, frac);
 }
 
 // (one warp) weighted median of the current 1-D problem (rows via row_key,
@@ -647,6 +669,212 @@ __device__ __noinline__ void select_fused(St& s, float cur, bool prior, float lo
   __syncwarp();
   if (lane == 0) { s.zstar = cur; s.owner = kNone; s.sel_fail = 1; }
   __syncwarp();
+}
+
+// ------------------------------------------------------------------ block-per-fit fused selection
+//
+// The same windowed weighted median with W = G / 32 warps sharing one fit
+// (long problems): warp w takes the row batches w, w + W, w + 2W, ... of
+// 32 * kPassU rows and compacts its keys inside the window into its own
+// sub-buffer of kSubCap entries; per-warp sums are combined in warp order.
+// The per-row factor (the column for axis steps, the edge products for the
+// polish) is read from global memory, the residual from shared memory.
+
+template <int G, int MODE>
+__device__ __noinline__ void fused_pass_blk(St& s, float lo, float hi) {
+  constexpr int W = G / 32;
+  const int lane = lane_id(), warp = gwarp<G>(), tid = gtid<G>();
+  const int n = s.n, nspec = s.nspec;
+  const float* __restrict__ xs = MODE == kAxis ? s.colp : s.vd;
+  const float bj = s.bj;
+  const int qc = s.qcode;
+  const uint32_t rr_s = smem_u32(s.rr);
+  float* __restrict__ bk = s.ck + warp * kSubCap;
+  float* __restrict__ bw = s.cw + warp * kSubCap;
+  int* __restrict__ bi = s.cid + warp * kSubCap;
+  const uint32_t bk_s = smem_u32(bk), bw_s = smem_u32(bw), bi_s = smem_u32(bi);
+  const unsigned lt = (1u << lane) - 1u;
+  float al = 0.f, ale = 0.f, at = 0.f, amin = kInf;
+  int base = 0;
+  for (int i0 = warp * 32 * kPassU; i0 < n; i0 += G * kPassU) {
+    float xv[kPassU], rv[kPassU];
+#pragma unroll
+    for (int u = 0; u < kPassU; ++u) {
+      const int e = i0 + u * 32 + lane;
+      xv[u] = e < n ? ldg_f(xs + e) : 0.f;
+      rv[u] = e < n ? lds_f(rr_s + 4u * e) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kPassU; ++u) {
+      if (i0 + u * 32 >= n) break;  // uniform
+      const int e = i0 + u * 32 + lane;
+      const float x = xv[u];  // zero beyond n: no weight, key +inf
+      const float w = fabsf(x);
+      float k;
+      if (MODE == kAxis) k = x != 0.f ? bj + __fdividef(rv[u], x) : kInf;
+      else k = e == qc ? 0.f : (x != 0.f ? __fdividef(rv[u], x) : kInf);
+      at += w;
+      al += k < lo ? w : 0.f;
+      ale += k <= hi ? w : 0.f;
+      amin = k > hi ? fminf(amin, k) : amin;
+      const bool in = e < n && k >= lo && k <= hi;
+      const unsigned msk = __ballot_sync(0xffffffffu, in);
+      if (msk) {
+        const int pos = base + __popc(msk & lt);
+        if (in && pos < kSubCap) {
+          sts_f(bk_s + 4u * pos, k);
+          sts_f(bw_s + 4u * pos, w);
+          sts_i(bi_s + 4u * pos, e);
+        }
+        base += __popc(msk);
+      }
+    }
+  }
+  if (warp == 0) {
+    for (int j0 = 0; j0 < nspec; j0 += 32) {
+      const int e = j0 + lane;
+      const bool v = e < nspec;
+      classify_one(bk, bw, bi, v ? s.sk[e] : kInf, v ? s.sw[e] : 0.f, v ? s.sid[e] : 0, v, lo, hi,
+                   al, ale, at, amin, base, kSubCap);
+    }
+  }
+  al = warp_sum(al);
+  ale = warp_sum(ale);
+  at = warp_sum(at);
+  amin = warp_min(amin);
+  if (lane == 0) {
+    s.redf[warp * 16 + 0] = al;
+    s.redf[warp * 16 + 1] = ale;
+    s.redf[warp * 16 + 2] = at;
+    s.redf[warp * 16 + 3] = amin;
+    s.wcnt[warp] = base;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = kInf;
+    int c = 0, ov = 0;
+    for (int w = 0; w < W; ++w) {
+      a0 += s.redf[w * 16 + 0];
+      a1 += s.redf[w * 16 + 1];
+      a2 += s.redf[w * 16 + 2];
+      a3 = fminf(a3, s.redf[w * 16 + 3]);
+      c += s.wcnt[w];
+      ov |= s.wcnt[w] > kSubCap;
+    }
+    s.p_wl = a0; s.p_wi = a1; s.p_wt = a2; s.p_amin = a3; s.p_cnt = c; s.p_ovf = ov;
+  }
+  __syncthreads();
+}
+
+// Move the buffered keys of every warp (up to kSubCap each) to the front of
+// the selection buffer, in warp order.  Returns their number.
+template <int G>
+__device__ __forceinline__ int compact_sub(St& s) {
+  constexpr int W = G / 32, kPer = kSubCap / 32;
+  const int lane = lane_id(), warp = gwarp<G>();
+  int pre = 0, tot = 0;
+  for (int w = 0; w < W; ++w) {
+    const int c = min(s.wcnt[w], kSubCap);
+    if (w < warp) pre += c;
+    tot += c;
+  }
+  const int c = min(s.wcnt[warp], kSubCap);
+  float k[kPer], wv[kPer];
+  int id[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int e = u * 32 + lane;
+    if (e < c) {
+      k[u] = s.ck[warp * kSubCap + e];
+      wv[u] = s.cw[warp * kSubCap + e];
+      id[u] = s.cid[warp * kSubCap + e];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int e = u * 32 + lane;
+    if (e < c) { s.ck[pre + e] = k[u]; s.cw[pre + e] = wv[u]; s.cid[pre + e] = id[u]; }
+  }
+  __syncthreads();
+  return tot;
+}
+
+// (warp 0) window from keys spread over the warps' sub-buffers.
+template <int G>
+__device__ __noinline__ void sub_window(St& s, float rl, float ru, float frac) {
+  constexpr int W = G / 32, kPerW = 32 / W;
+  const int lane = lane_id();
+  const int w = lane % W, r = lane / W;
+  const int c = min(s.wcnt[w], kSubCap);
+  float k = kInf, wt = 0.f;
+  if (c > 0) {
+    const int e = (r * c) / kPerW;
+    k = s.ck[w * kSubCap + e];
+    wt = s.cw[w * kSubCap + e];
+  }
+  window_from_samples(s, k, wt, rl, ru, frac);
+}
+
+// Block version of select_fused (same contract).
+template <int G, int MODE>
+__device__ __noinline__ void select_fused_blk(St& s, float cur, bool prior, float lo0, float hi0) {
+  const int tid = gtid<G>(), warp = gwarp<G>();
+  float rl = -kInf, ru = kInf;  // open interval known to hold the target
+  float wrl = 0.f, wru = -1.f;  // weight of keys <= rl, < ru
+  float lo = lo0, hi = hi0;
+  gsync<G>();
+  if (!prior) {
+    if (warp == 0) region_window<MODE>(s, rl, ru, 0.5f, 0);
+    gsync<G>();
+    lo = s.lo; hi = s.hi;
+  }
+  float half = -1.f;
+  if (tid == 0) s.selects++;
+  for (int it = 0; it < kMaxPasses; ++it) {
+    fused_pass_blk<G, MODE>(s, lo, hi);
+    if (tid == 0) s.passes++;
+    const float wl = s.p_wl, wle = s.p_wi, wt = s.p_wt, amin = s.p_amin;
+    const int cnt = s.p_cnt, ovf = s.p_ovf;
+    if (half < 0.f) {
+      if (!(wt > 0.f)) {
+        gsync<G>();
+        if (tid == 0) { s.zstar = cur; s.owner = kNone; }
+        gsync<G>();
+        return;
+      }
+      half = 0.5f * wt;
+      wru = wt;
+    }
+    if (half <= wl) {                       // target below the window
+      ru = lo; wru = wl;
+      if (warp == 0) region_window<MODE>(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
+    } else if (half > wle) {                // target above the window
+      rl = hi; wrl = wle;
+      if (warp == 0) region_window<MODE>(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
+    } else if (!ovf) {                      // target inside, all keys buffered
+      compact_sub<G>(s);
+      select_buf<G>(s, cnt, cur, 0, wl, half, amin, wle - wl);
+      return;
+    } else {                                // inside but too many keys: narrow
+      rl = next_down(lo); ru = next_up(hi); wrl = wl; wru = wle;
+      if (warp == 0) sub_window<G>(s, rl, ru, (half - wl) / fmaxf(wle - wl, 1e-30f));
+      gsync<G>();
+      if (s.lo == lo && s.hi == hi) {
+        // no narrower window from the samples (keys tie at the ends): finish
+        // on the buffered keys
+        const int m = compact_sub<G>(s);
+        select_buf<G>(s, m, cur, 0, wl, half, amin, wle - wl);
+        return;
+      }
+    }
+    gsync<G>();
+    lo = s.lo; hi = s.hi;
+    if (!(lo <= hi)) break;  // empty interval: only reachable through inconsistent input
+  }
+  gsync<G>();
+  if (tid == 0) { s.zstar = cur; s.owner = kNone; s.sel_fail = 1; }
+  gsync<G>();
 }
 
 // ------------------------------------------------------------------ warp-0 algebra
@@ -815,8 +1043,26 @@ __device__ __noinline__ void lu_solve_t(St& s, float* x) {
 // (one warp) form the basis matrix, factor it and snap b onto the basis
 // hyperplanes (phantom coordinates keep their value).  Sets s.flag.
 __device__ __noinline__ void snap(St& s) {
-  const int lane = lane_id(), p = s.p;
-  for (int k = 0; k < p; ++k) normal_to(s, s.code[k], s.Bm + k * p);
+  const int lane = lane_id(), p = s.p, pp = p * p;
+  // basis matrix rows = constraint normals; element (k, c) of a row
+  // constraint is x_{code_k, c}: strided loads, issued 8 per lane at a time
+  for (int e0 = 0; e0 < pp; e0 += 32 * 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 32 + lane;
+      v[u] = 0.f;
+      if (e < pp) {
+        const int k = e / p, c = e - k * p, cd = s.code[k];
+        v[u] = cd >= 0 ? xval(s, c, cd) : (c == -cd - 1 ? 1.f : 0.f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 32 + lane;
+      if (e < pp) s.Bm[e] = v[u];
+    }
+  }
   for (int k = lane; k < p; k += 32) {
     int cd = s.code[k];
     s.hv[k] = cd >= 0 ? s.yq[cd] : (s.phan[k] ? s.bv[-cd - 1] : 0.f);
@@ -953,6 +1199,40 @@ __device__ __forceinline__ void axpy_r(St& s, const float* __restrict__ col, flo
   }
 }
 
+// v_i = x_i . d for the edge direction d into `vd` (shared for one warp,
+// global scratch for a block), zero on basis rows other than the released
+// one (they stay on their hyperplanes along the edge).  Column loads
+// batched kPassU per thread.
+template <int G>
+__device__ __forceinline__ void edge_products(St& s, float* __restrict__ vd) {
+  const int n = s.n, p = s.p, lane = gtid<G>(), qc = s.qcode;
+  const float* __restrict__ dv = s.dv;
+  const unsigned* __restrict__ mask = s.mask;
+  for (int i0 = 0; i0 < n; i0 += G * kPassU) {
+    float v[kPassU];
+#pragma unroll
+    for (int u = 0; u < kPassU; ++u) v[u] = 0.f;
+    for (int c = 0; c < p; ++c) {
+      const float dc = dv[c];
+      if (dc == 0.f) continue;  // uniform; d is zero on basis coordinates
+      const float* __restrict__ col = colptr(s, c);
+#pragma unroll
+      for (int u = 0; u < kPassU; ++u) {
+        const int i = i0 + u * G + lane;
+        if (i < n) v[u] += col[i] * dc;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPassU; ++u) {
+      const int i = i0 + u * G + lane;
+      if (i < n) {
+        const bool inb = (mask[i >> 5] >> (i & 31)) & 1u;
+        vd[i] = inb && i != qc ? 0.f : v[u];
+      }
+    }
+  }
+}
+
 // (one warp) start copying column j into column buffer `buf` (16-byte
 // asynchronous copies; the gathered column is 16-byte aligned and padded
 // to a multiple of 4 floats).
@@ -975,34 +1255,6 @@ __device__ __forceinline__ float objective(St& s) {
   return as + s.lam * bs;
 }
 
-// Block path: write the breakpoints of all rows (and the specials after
-// them) into the buffer, then select over the buffer.
-template <int G, int MODE>
-__device__ __forceinline__ void select_staged(St& s, float cur) {
-  const int n = s.n;
-  for (int i = gtid<G>(); i < n; i += G) {
-    float k, w;
-    row_key<MODE>(s, i, k, w);
-    s.ck[i] = k;
-    s.cw[i] = w;
-  }
-  for (int e = gtid<G>(); e < s.nspec; e += G) {
-    s.ck[n + e] = s.sk[e]; s.cw[n + e] = s.sw[e]; s.cid[n + e] = s.sid[e];
-  }
-  gsync<G>();
-  float ws = 0.f;
-  for (int e = gtid<G>(); e < n + s.nspec; e += G) ws += s.cw[e];
-  float dummy;
-  const float W = gsum2<G>(s, ws, 0.f, dummy);
-  gsync<G>();
-  if (!(W > 0.f)) {
-    if (gtid<G>() == 0) { s.zstar = cur; s.owner = kNone; }
-    gsync<G>();
-    return;
-  }
-  select_buf<G>(s, n + s.nspec, cur, 1, 0.f, 0.5f * W, kInf, W);
-}
-
 // Exact minimisation along axis j (Section 3.3): the weighted median of
 // z_i = b_j + r_i / x_ij (weights |x_ij|) and 0 (weight lambda).  Returns
 // the move; records the breakpoint landed on in piv[j].
@@ -1016,6 +1268,11 @@ __device__ __noinline__ float axis_update(St& s, int j, int jnext) {
     __syncwarp();
     if (jnext >= 0) prefetch_col(s, jnext, s.cur ^ 1);
     col = s.cb[s.cur];
+  } else if (jnext >= 0) {
+    // block path: the columns stream from global memory; pull the next
+    // one into L2 while this step runs
+    const float* nx = colptr(s, jnext);
+    for (int o = gtid<G>() * 32; o < s.ld; o += G * 32) prefetch_l2(nx + o);
   }
   gsync<G>();
   if (gtid<G>() == 0) {
@@ -1025,11 +1282,10 @@ __device__ __noinline__ float axis_update(St& s, int j, int jnext) {
     s.sk[0] = 0.f; s.sw[0] = s.lam; s.sid[0] = coord_code(j);
   }
   gsync<G>();
-  if (G == 32) {
+  {
     const float dl = s.dl[j];
-    select_fused<kAxis>(s, bj, true, bj - dl, bj + dl);
-  } else {
-    select_staged<G, kAxis>(s, bj);
+    if (G == 32) select_fused<kAxis>(s, bj, true, bj - dl, bj + dl);
+    else select_fused_blk<G, kAxis>(s, bj, true, bj - dl, bj + dl);
   }
   const float z = s.zstar;
   const int own = s.owner;
@@ -1127,14 +1383,30 @@ __device__ __noinline__ void chop(St& s, int k, int& sweeps, int& probes) {
   }
   float lo = pa, hi = pe;
   int np = 0;
-  while (hi - lo > o.chop_tol * scale && np + 2 <= o.chop_max_probes) {
-    float m1 = lo + (hi - lo) / 3.f, m2 = hi - (hi - lo) / 3.f;
-    float g1 = probe<G>(s, k, m1, best_f, sweeps, probes);
-    float g2 = probe<G>(s, k, m2, best_f, sweeps, probes);
-    np += 2;
-    if (g1 < g2) hi = m2;
-    else if (g1 > g2) lo = m1;
-    else { lo = m1; hi = m2; }
+  if (o.chop_sections == 4) {
+    // four sections, probes at the inner points; keep the two sections
+    // around the lowest probe (leftmost on ties)
+    while (hi - lo > o.chop_tol * scale && np + 3 <= o.chop_max_probes) {
+      const float h = (hi - lo) / 4.f;
+      const float t1 = lo + h, t2 = lo + 2.f * h, t3 = hi - h;
+      const float g1 = probe<G>(s, k, t1, best_f, sweeps, probes);
+      const float g2 = probe<G>(s, k, t2, best_f, sweeps, probes);
+      const float g3 = probe<G>(s, k, t3, best_f, sweeps, probes);
+      np += 3;
+      if (g1 <= g2 && g1 <= g3) hi = t2;
+      else if (g2 <= g3) { lo = t1; hi = t3; }
+      else lo = t2;
+    }
+  } else {
+    while (hi - lo > o.chop_tol * scale && np + 2 <= o.chop_max_probes) {
+      float m1 = lo + (hi - lo) / 3.f, m2 = hi - (hi - lo) / 3.f;
+      float g1 = probe<G>(s, k, m1, best_f, sweeps, probes);
+      float g2 = probe<G>(s, k, m2, best_f, sweeps, probes);
+      np += 2;
+      if (g1 < g2) hi = m2;
+      else if (g1 > g2) lo = m1;
+      else { lo = m1; hi = m2; }
+    }
   }
   for (int c = gtid<G>(); c < s.p; c += G) s.bv[c] = s.bbest[c];
   gsync<G>();
@@ -1146,10 +1418,14 @@ __device__ __noinline__ void chop(St& s, int k, int& sweeps, int& probes) {
 template <int G>
 __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonunique) {
   const int tid = gtid<G>(), lane = lane_id(), warp = gwarp<G>();
-  const int n = s.n, p = s.p, ld = s.ld;
+  const int n = s.n, p = s.p;
   int it = 0;
   *is_opt = 0;
   *nonunique = 0;
+  if (G == 32) {
+    cp_async_wait_all();  // the column buffers hold edge products below
+    __syncwarp();
+  }
   for (;;) {
     if (warp == 0) snap(s);
     gsync<G>();
@@ -1161,12 +1437,24 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
       for (int k = 0; k < p; ++k)
         if (s.code[k] >= 0) s.mask[s.code[k] >> 5] |= 1u << (s.code[k] & 31);
     gsync<G>();
-    // column sums g_c = -sum_{rows not in basis} sign(r_i) x_ic
+    // column sums g_c = -sum_{rows not in basis} sign(r_i) x_ic (loads
+    // batched kPassU per thread; per-thread order is row order)
     for (int c = 0; c < p; ++c) {
-      const float* col = colptr(s, c);
+      const float* __restrict__ col = colptr(s, c);
       float a = 0.f;
-      for (int i = tid; i < n; i += G)
-        if (!((s.mask[i >> 5] >> (i & 31)) & 1u)) a -= fsign(s.rr[i]) * col[i];
+      for (int i0 = 0; i0 < n; i0 += G * kPassU) {
+        float xv[kPassU];
+#pragma unroll
+        for (int u = 0; u < kPassU; ++u) {
+          const int i = i0 + u * G + tid;
+          xv[u] = i < n ? col[i] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kPassU; ++u) {
+          const int i = i0 + u * G + tid;
+          if (i < n && !((s.mask[i >> 5] >> (i & 31)) & 1u)) a -= fsign(s.rr[i]) * xv[u];
+        }
+      }
       a = warp_sum(a);
       if (lane == 0) s.red2[warp * p + c] = a;
     }
@@ -1182,8 +1470,17 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
       s.nspec = edge_specials(s, q);
     }
     gsync<G>();
-    if (G == 32) select_fused<kEdge>(s, 0.f, false, 0.f, 0.f);
-    else select_staged<G, kEdge>(s, 0.f);
+    {
+      float* vd = G == 32 ? s.cb[0] : s.vdg;
+      edge_products<G>(s, vd);
+      gsync<G>();
+      if (tid == 0) s.vd = vd;
+      gsync<G>();
+      if (G == 32) select_fused<kEdge>(s, 0.f, false, 0.f, 0.f);
+      else select_fused_blk<G, kEdge>(s, 0.f, false, 0.f, 0.f);
+      if (tid == 0) s.vd = nullptr;
+      gsync<G>();
+    }
     const float ts = s.zstar;
     const int own = s.owner;
     if (own == kNone) break;  // flat along the edge (cannot happen when F decreases)
@@ -1197,6 +1494,45 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
   }
   gsync<G>();
   return it;
+}
+
+// F at the vertex of the current basis (snap; +inf when singular).
+template <int G>
+__device__ __noinline__ float vertex_objective(St& s) {
+  if (gwarp<G>() == 0) snap(s);
+  gsync<G>();
+  if (!s.flag) return kInf;
+  recompute_r<G>(s);
+  gsync<G>();
+  return objective<G>(s);
+}
+
+template <int G>
+__device__ __forceinline__ void copy_basis(St& s, int* cd, int* ph, const int* cs, const int* ps) {
+  gsync<G>();
+  for (int k = gtid<G>(); k < s.p; k += G) { cd[k] = cs[k]; ph[k] = ps[k]; }
+  gsync<G>();
+}
+
+// Polish start: the basis built at the descent point, or the previous path
+// position's final basis when its vertex has the lower objective at this
+// lambda (along a path the optimal basis changes by a few hyperplanes, the
+// descent point's basis can be many pivots away).  The descent point
+// itself is kept in bbest for the fallback.
+template <int G>
+__device__ __noinline__ void choose_polish_start(St& s) {
+  if (gwarp<G>() == 0) build_basis(s);
+  gsync<G>();
+  if (!s.has_prev) return;
+  for (int c = gtid<G>(); c < s.p; c += G) s.bbest[c] = s.bv[c];
+  const float fa = vertex_objective<G>(s);
+  copy_basis<G>(s, s.code_alt, s.phan_alt, s.code, s.phan);
+  for (int c = gtid<G>(); c < s.p; c += G) s.bv[c] = s.bbest[c];  // phantoms keep descent values
+  copy_basis<G>(s, s.code, s.phan, s.code_prev, s.phan_prev);
+  const float fb = vertex_objective<G>(s);
+  if (!(fb < fa)) copy_basis<G>(s, s.code, s.phan, s.code_alt, s.phan_alt);
+  for (int c = gtid<G>(); c < s.p; c += G) s.bv[c] = s.bbest[c];
+  gsync<G>();
 }
 
 // ------------------------------------------------------------------ one problem
@@ -1236,13 +1572,38 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
   if (ok) {
     ld = (int)xg_ld(n);
     Xw = A.Xg + xg_base(o0, q, A.P4);
-    for (int64_t e = tid; e < (int64_t)n * p; e += G) {
-      int c = (int)(e / n), i = (int)(e % n);
-      int64_t row = A.row_idx ? (int64_t)A.row_idx[o0 + i] : o0 + i;
-      if (row < 0 || row >= A.rows_X) { bad = 1; continue; }
-      float v = A.X[row * A.ldX + c];
-      if (!isfinite(v)) bad = 1;
-      Xw[(int64_t)c * ld + i] = v;
+    if (G == 32) {
+      // short problems: rows of the shared design sit in L2
+      for (int64_t e = tid; e < (int64_t)n * p; e += G) {
+        int c = (int)(e / n), i = (int)(e % n);
+        int64_t row = A.row_idx ? (int64_t)A.row_idx[o0 + i] : o0 + i;
+        if (row < 0 || row >= A.rows_X) { bad = 1; continue; }
+        float v = A.X[row * A.ldX + c];
+        if (!isfinite(v)) bad = 1;
+        Xw[(int64_t)c * ld + i] = v;
+      }
+    } else {
+      // long problems: transpose 32 rows at a time through shared memory
+      // (the basis-matrix area), reading rows and writing columns coalesced
+      float* tile = s.Bm;  // >= 33 * P floats
+      for (int i0 = 0; i0 < n; i0 += 32) {
+        const int rows = min(32, n - i0);
+        for (int e = tid; e < rows * p; e += G) {
+          const int i = e / p, c = e - i * p;
+          const int64_t row = A.row_idx ? (int64_t)A.row_idx[o0 + i0 + i] : o0 + i0 + i;
+          float v = 0.f;
+          if (row < 0 || row >= A.rows_X) bad = 1;
+          else v = A.X[row * A.ldX + c];
+          if (!isfinite(v)) bad = 1;
+          tile[c * 33 + i] = v;
+        }
+        __syncthreads();
+        for (int e = tid; e < p * 32; e += G) {
+          const int c = e >> 5, i = e & 31;
+          if (i < rows) Xw[(int64_t)c * ld + i0 + i] = tile[c * 33 + i];
+        }
+        __syncthreads();
+      }
     }
     for (int i = tid; i < n; i += G) if (!isfinite(A.y[o0 + i])) bad = 1;
   }
@@ -1257,9 +1618,11 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
   if (tid == 0) {
     s.n = n; s.p = p; s.ld = ld;
     s.Xq = Xw; s.yq = A.y + o0;
+    s.vdg = Xw + (int64_t)A.P4 * ld;  // the spare column slot
   }
   gsync<G>();
   for (int c = tid; c < p; c += G) s.bv[c] = A.b_init ? A.b_init[(int64_t)q * A.P + c] : 0.f;
+  if (tid == 0) s.has_prev = 0;
   gsync<G>();
   recompute_r<G>(s);
   gsync<G>();
@@ -1315,11 +1678,14 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
       if (is_opt) flags |= 4;
     }
     if (!is_opt && A.o.polish) {
-      if (gwarp<G>() == 0) build_basis(s);
-      gsync<G>();
+      choose_polish_start<G>(s);
       const int mp = A.o.max_pivots > 0 ? A.o.max_pivots : 4 * p + 64;
       pivots = polish<G>(s, mp, &is_opt, &nonu);
       if (!is_opt) status |= kFitMaxIters;
+    }
+    if (is_opt) {  // warm start for the next path position's polish
+      copy_basis<G>(s, s.code_prev, s.phan_prev, s.code, s.phan);
+      if (tid == 0) s.has_prev = 1;
     }
     t1 = clock64(); t_vx += t1 - t0;
     if (is_opt && nonu) status |= kFitNonunique;
@@ -1342,23 +1708,26 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
 template <int G>
 __host__ __device__ size_t group_smem_bytes(int ncap, int P) {
   constexpr int W = G / 32;
-  size_t cap = G == 32 ? (size_t)kBufCap : (size_t)ncap + P + 1;
-  // one warp: the basis matrix overlays the selection buffer (never live
-  // together: the polish rebuilds it after every edge line search)
-  size_t sel_bm = G == 32 ? (3 * cap > (size_t)P * P ? 3 * cap : (size_t)P * P)
-                          : 3 * cap + (size_t)P * P;
+  size_t cap = G == 32 ? (size_t)kBufCap : (size_t)W * kSubCap;
+  // the basis matrix overlays the selection buffer (never live together:
+  // the polish rebuilds it after every edge line search); the block path's
+  // gather also stages 32 x P tiles there
+  size_t sel_bm = 3 * cap > (size_t)P * P ? 3 * cap : (size_t)P * P;
+  if (G > 32 && sel_bm < 33 * (size_t)P) sel_bm = 33 * (size_t)P;
   size_t colbuf = G == 32 ? 2 * (size_t)ncap : 0;
   size_t words = (size_t)ncap + colbuf + sel_bm + 7 * (size_t)P + (size_t)W * P +
-                 5 * (size_t)P + 3 * ((size_t)P + 1) + (size_t)ncap / 32 + 1 +
-                 2 * (size_t)W * 16 + 64;
+                 9 * (size_t)P + 3 * ((size_t)P + 1) + (size_t)ncap / 32 + 1 +
+                 2 * (size_t)W * 16 + 64 + W;
   return ((words * 4 + 15) / 16) * 16;
 }
 
 template <int G>
 __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   constexpr int W = G / 32;
-  s.cap = G == 32 ? kBufCap : ncap + P + 1;
+  s.cap = G == 32 ? kBufCap : W * kSubCap;
   s.maskw = ncap / 32 + 1;
+  s.vd = nullptr;
+  s.vdg = nullptr;
   float* f = reinterpret_cast<float*>(raw);
   s.rr = f; f += ncap;
   if (G == 32) { s.cb[0] = f; f += ncap; s.cb[1] = f; f += ncap; }
@@ -1367,11 +1736,11 @@ __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   s.ck = f; f += s.cap;
   s.cw = f; f += s.cap;
   s.cid = reinterpret_cast<int*>(f); f += s.cap;
-  if (G == 32) {
-    s.Bm = sel;  // overlay (see group_smem_bytes)
-    if (P * P > 3 * s.cap) f = sel + P * P;
-  } else {
-    s.Bm = f; f += P * P;
+  s.Bm = sel;  // overlay (see group_smem_bytes)
+  {
+    int sel_bm = 3 * s.cap > P * P ? 3 * s.cap : P * P;
+    if (G > 32 && sel_bm < 33 * P) sel_bm = 33 * P;
+    f = sel + sel_bm;
   }
   s.bv = f; f += P; s.bbest = f; f += P; s.dv = f; f += P;
   s.mu = f; f += P; s.tv = f; f += P; s.hv = f; f += P; s.dl = f; f += P;
@@ -1379,6 +1748,8 @@ __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   int* ip = reinterpret_cast<int*>(f);
   s.code = ip; ip += P; s.phan = ip; ip += P; s.piv = ip; ip += P; s.perm = ip; ip += P;
   s.pcol = ip; ip += P;
+  s.code_prev = ip; ip += P; s.phan_prev = ip; ip += P;
+  s.code_alt = ip; ip += P; s.phan_alt = ip; ip += P;
   f = reinterpret_cast<float*>(ip);
   s.sk = f; f += P + 1; s.sw = f; f += P + 1;
   s.sid = reinterpret_cast<int*>(f); f += P + 1;
@@ -1387,6 +1758,7 @@ __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   s.redi = reinterpret_cast<int*>(f); f += W * 16;
   s.sampk = f; f += 32;
   s.sampw = f; f += 32;
+  s.wcnt = reinterpret_cast<int*>(f); f += W;
 }
 
 template <int G, int NW>
@@ -1445,8 +1817,7 @@ int fit_block_max_rows(int G, int P) {
   int lo = 0, hi = 1 << 16;
   while (lo < hi) {
     int mid = (lo + hi + 1) / 2;
-    size_t b = G == 32 ? group_smem_bytes<32>(mid, P) : G == 64 ? group_smem_bytes<64>(mid, P)
-             : G == 128 ? group_smem_bytes<128>(mid, P) : group_smem_bytes<256>(mid, P);
+    size_t b = G == 32 ? group_smem_bytes<32>(mid, P) : group_smem_bytes<kBlockG>(mid, P);
     if (b <= limit) lo = mid; else hi = mid - 1;
   }
   return lo;
@@ -1454,25 +1825,39 @@ int fit_block_max_rows(int G, int P) {
 
 // Default group size for a problem set: one warp per fit while its rows fit
 // a warp's share of shared memory, else a block per fit.
-int fit_block_group(int n_max) { return n_max <= 8192 ? 32 : 128; }
+int fit_block_group(int n_max) { return n_max <= 8192 ? 32 : kBlockG; }
 
-cudaError_t launch_fit_block(const FitArgs& a, cudaStream_t st, int num_sms, int G) {
-  int ncap = (a.n_max + 31) & ~31;
-  if (ncap < 32) ncap = 32;
+// Group size a call asks for (dims->group_threads), 0 when invalid.
+int launch_group(const ladlasso_dims* d) {
+  if (d->group_threads == 0) return fit_block_group(d->n_max);
+  return d->group_threads == 32 || d->group_threads == kBlockG ? d->group_threads : 0;
+}
+
+static int row_cap(int n_max) {
+  int ncap = (n_max + 31) & ~31;
+  return ncap < 32 ? 32 : ncap;
+}
+
+// Fits per thread block for group size G: one-warp groups, as many as
+// shared memory allows (at most 16, at most `fits_per_block` when > 0);
+// one block per fit otherwise.
+int fit_block_fits_per_block(int G, int P, int n_max, int fits_per_block) {
+  if (G != 32) return 1;
+  const size_t per = group_smem_bytes<32>(row_cap(n_max), P);
+  int nw = (int)(kDynSmemLimit / (per ? per : 1));
+  if (nw > 16) nw = 16;
+  if (fits_per_block > 0 && nw > fits_per_block) nw = fits_per_block;
+  return nw < 1 ? 1 : nw;
+}
+
+cudaError_t launch_fit_block(const FitArgs& a, cudaStream_t st, int num_sms, int G,
+                             int fits_per_block) {
+  const int ncap = row_cap(a.n_max);
   switch (G) {
-    case 32: {
-      // one block per SM holding as many one-warp fits as shared memory
-      // allows (up to 16)
-      const size_t per = group_smem_bytes<32>(ncap, a.P);
-      const size_t limit = kDynSmemLimit;
-      int nw = (int)(limit / (per ? per : 1));
-      if (nw > 16) nw = 16;
-      if (nw < 1) nw = 1;
-      return launch_variant<32, 16>(a, st, num_sms, ncap, nw);
-    }
-    case 64: return launch_variant<64, 1>(a, st, num_sms, ncap, 1);
-    case 128: return launch_variant<128, 1>(a, st, num_sms, ncap, 1);
-    case 256: return launch_variant<256, 1>(a, st, num_sms, ncap, 1);
+    case 32:
+      return launch_variant<32, 16>(a, st, num_sms, ncap,
+                                    fit_block_fits_per_block(32, a.P, a.n_max, fits_per_block));
+    case kBlockG: return launch_variant<kBlockG, 1>(a, st, num_sms, ncap, 1);
     default: return cudaErrorInvalidValue;
   }
 }

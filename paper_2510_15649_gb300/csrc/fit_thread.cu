@@ -28,6 +28,8 @@ struct TFit {
   float* Bm;   // [P * P]
   float* bv; float* bbest; float* dv; float* mu; float* hv; float* tv;  // [P]
   int* code; int* phan; int* piv; int* perm; int* pcol;  // [P]
+  int* code_prev; int* phan_prev; int* code_alt; int* phan_alt;  // [P]
+  int has_prev;
 
   __device__ __forceinline__ float x(int i, int c) const { return Xq[(int64_t)c * ld + i]; }
   __device__ float yv(int i) const { return a->y[off0 + i]; }
@@ -190,14 +192,28 @@ struct TFit {
     }
     float lo = pa, hi = pe;
     int np = 0;
-    while (hi - lo > o.chop_tol * scale && np + 2 <= o.chop_max_probes) {
-      float m1 = lo + (hi - lo) / 3.f, m2 = hi - (hi - lo) / 3.f;
-      float g1 = probe(k, m1, best_f, sweeps, probes);
-      float g2 = probe(k, m2, best_f, sweeps, probes);
-      np += 2;
-      if (g1 < g2) hi = m2;
-      else if (g1 > g2) lo = m1;
-      else { lo = m1; hi = m2; }
+    if (o.chop_sections == 4) {
+      while (hi - lo > o.chop_tol * scale && np + 3 <= o.chop_max_probes) {
+        const float h = (hi - lo) / 4.f;
+        const float t1 = lo + h, t2 = lo + 2.f * h, t3 = hi - h;
+        const float g1 = probe(k, t1, best_f, sweeps, probes);
+        const float g2 = probe(k, t2, best_f, sweeps, probes);
+        const float g3 = probe(k, t3, best_f, sweeps, probes);
+        np += 3;
+        if (g1 <= g2 && g1 <= g3) hi = t2;
+        else if (g2 <= g3) { lo = t1; hi = t3; }
+        else lo = t2;
+      }
+    } else {
+      while (hi - lo > o.chop_tol * scale && np + 2 <= o.chop_max_probes) {
+        float m1 = lo + (hi - lo) / 3.f, m2 = hi - (hi - lo) / 3.f;
+        float g1 = probe(k, m1, best_f, sweeps, probes);
+        float g2 = probe(k, m2, best_f, sweeps, probes);
+        np += 2;
+        if (g1 < g2) hi = m2;
+        else if (g1 > g2) lo = m1;
+        else { lo = m1; hi = m2; }
+      }
     }
     for (int c = 0; c < p; ++c) bv[c] = bbest[c];
     recompute_r();
@@ -297,22 +313,46 @@ struct TFit {
     return false;
   }
 
+  // b := the vertex of the current basis (phantom coordinates keep their
+  // value), r recomputed.  False when the basis matrix is singular.
+  __device__ bool snap() {
+    for (int k = 0; k < p; ++k) {
+      normal_to(code[k], Bm + k * p);
+      int cd = code[k];
+      hv[k] = cd >= 0 ? yv(cd) : (phan[k] ? bv[-cd - 1] : 0.f);
+    }
+    if (!lu()) return false;
+    lu_solve(hv);
+    for (int c = 0; c < p; ++c) bv[c] = hv[c];
+    for (int k = 0; k < p; ++k) if (code[k] < 0 && !phan[k]) bv[-code[k] - 1] = 0.f;
+    recompute_r();
+    return true;
+  }
+
+  // Polish start: the descent point's basis, or the previous path
+  // position's final basis when its vertex has the lower objective here.
+  __device__ void choose_polish_start() {
+    build_basis();
+    if (!has_prev) return;
+    for (int c = 0; c < p; ++c) bbest[c] = bv[c];
+    const float fa = snap() ? objective() : kInf;
+    for (int k = 0; k < p; ++k) { code_alt[k] = code[k]; phan_alt[k] = phan[k]; }
+    for (int c = 0; c < p; ++c) bv[c] = bbest[c];
+    for (int k = 0; k < p; ++k) { code[k] = code_prev[k]; phan[k] = phan_prev[k]; }
+    const float fb = snap() ? objective() : kInf;
+    if (!(fb < fa))
+      for (int k = 0; k < p; ++k) { code[k] = code_alt[k]; phan[k] = phan_alt[k]; }
+    for (int c = 0; c < p; ++c) bv[c] = bbest[c];
+    recompute_r();
+  }
+
   __device__ int polish(int max_piv, int& is_opt, int& nonunique) {
     const float tol = a->o.tol_opt * fmaxf(1.f, lam);
     int it = 0;
     is_opt = 0;
     nonunique = 0;
     for (;;) {
-      for (int k = 0; k < p; ++k) {
-        normal_to(code[k], Bm + k * p);
-        int cd = code[k];
-        hv[k] = cd >= 0 ? yv(cd) : (phan[k] ? bv[-cd - 1] : 0.f);
-      }
-      if (!lu()) break;
-      lu_solve(hv);
-      for (int c = 0; c < p; ++c) bv[c] = hv[c];
-      for (int k = 0; k < p; ++k) if (code[k] < 0 && !phan[k]) bv[-code[k] - 1] = 0.f;
-      recompute_r();
+      if (!snap()) break;
       for (int c = 0; c < p; ++c) mu[c] = 0.f;
       for (int i = 0; i < n; ++i) {
         if (in_basis_row(i)) continue;
@@ -385,6 +425,7 @@ struct TFit {
   __device__ void run() {
     const FitArgs& A = *a;
     for (int c = 0; c < p; ++c) bv[c] = A.b_init ? A.b_init[(int64_t)q * A.P + c] : 0.f;
+    has_prev = 0;
     recompute_r();
     for (int l = 0; l < A.L; ++l) {
       int64_t f = (int64_t)q * A.L + l;
@@ -422,10 +463,14 @@ struct TFit {
         if (is_opt) flags |= 4;
       }
       if (!is_opt && A.o.polish) {
-        build_basis();
+        choose_polish_start();
         int mp = A.o.max_pivots > 0 ? A.o.max_pivots : 4 * p + 64;
         pivots = polish(mp, is_opt, nonu);
         if (!is_opt) status |= kFitMaxIters;
+      }
+      if (is_opt) {
+        for (int k = 0; k < p; ++k) { code_prev[k] = code[k]; phan_prev[k] = phan[k]; }
+        has_prev = 1;
       }
       if (is_opt && nonu) status |= kFitNonunique;
       float F = objective();
@@ -492,6 +537,8 @@ __global__ void __launch_bounds__(128) fit_thread_kernel(FitArgs args) {
   t.bv = v; t.bbest = v + P; t.dv = v + 2 * P; t.mu = v + 3 * P; t.hv = v + 4 * P; t.tv = v + 5 * P;
   int* iv = reinterpret_cast<int*>(v + 6 * P);
   t.code = iv; t.phan = iv + P; t.piv = iv + 2 * P; t.perm = iv + 3 * P; t.pcol = iv + 4 * P;
+  t.code_prev = iv + 5 * P; t.phan_prev = iv + 6 * P; t.code_alt = iv + 7 * P;
+  t.phan_alt = iv + 8 * P;  // 6 P floats + 9 P ints <= the 16 P per-problem slots
   t.run();
 }
 

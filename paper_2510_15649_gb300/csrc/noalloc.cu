@@ -11,7 +11,9 @@
 #include "common.cuh"
 
 namespace ll {
-cudaError_t launch_fit_block(const FitArgs& a, cudaStream_t st, int num_sms, int G);
+cudaError_t launch_fit_block(const FitArgs& a, cudaStream_t st, int num_sms, int G,
+                             int fits_per_block);
+int launch_group(const ladlasso_dims* d);
 cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t total_rows, int* ctrl,
                                     cudaStream_t st);
 cudaError_t launch_order(const int64_t* offsets, const int32_t* nr, const int32_t* p, int P, int B,
@@ -60,9 +62,11 @@ extern "C" int ladlasso_fit_batched_noalloc(const float* X, const float* y, cons
   if (!row_idx && d->total_rows > d->rows_X) return LADLASSO_ERR_INVALID;
   // scratch needed: control words, work order, gathered designs (see common.cuh)
   const size_t P4 = ((size_t)d->P_cols + 3) & ~(size_t)3;
-  const size_t need = ws_xg_offset(d->B) + ((size_t)d->total_rows + 4 * (size_t)d->B) * P4 * sizeof(float);
+  const size_t need = ws_xg_offset(d->B) + ((size_t)d->total_rows + 4 * (size_t)d->B) *
+                                                (size_t)xg_slots((int)P4) * sizeof(float);
   if (need > kScratchBytes) return LADLASSO_ERR_NOMEM;  // problem set too large for the fixed array
-  const int G = fit_block_group(d->n_max);
+  const int G = launch_group(d);
+  if (G == 0 || d->fits_per_block < 0) return LADLASSO_ERR_INVALID;
   if (d->n_max > fit_block_max_rows(G, d->P_cols)) return LADLASSO_ERR_NOMEM;
   if (d->B == 0) return LADLASSO_OK;
   unsigned char* base = nullptr;
@@ -86,11 +90,11 @@ extern "C" int ladlasso_fit_batched_noalloc(const float* X, const float* y, cons
   a.P4 = (int)P4;
   a.o = {o->tol_move, o->max_sweeps, o->chop, o->chop_bracket, o->chop_tol, o->chop_max_probes,
          o->chop_max_extend, o->probe_max_sweeps, o->polish, o->max_pivots, o->tol_opt,
-         o->lambda_min_floor};
+         o->lambda_min_floor, o->chop_sections};
   if (!(a.o.tol_move >= 0.f && a.o.max_sweeps >= 1 && a.o.chop_bracket > 0.f &&
         a.o.chop_tol >= 0.f && a.o.chop_max_probes >= 0 && a.o.chop_max_extend >= 0 &&
         a.o.probe_max_sweeps >= 1 && a.o.max_pivots >= 0 && a.o.tol_opt >= 0.f &&
-        a.o.lambda_min_floor >= 0.f))
+        a.o.lambda_min_floor >= 0.f && (a.o.chop_sections == 3 || a.o.chop_sections == 4)))
     return LADLASSO_ERR_INVALID;
 
   cudaStream_t st = (cudaStream_t)stream;
@@ -103,5 +107,6 @@ extern "C" int ladlasso_fit_batched_noalloc(const float* X, const float* y, cons
   if (launch_validate_offsets(offsets, a.B, a.total_rows, a.queue, st) != cudaSuccess)
     return LADLASSO_ERR_CUDA;
   if (launch_order(offsets, a.n_rows, a.p, a.P, a.B, a.order, st) != cudaSuccess) return LADLASSO_ERR_CUDA;
-  return launch_fit_block(a, st, sms, G) == cudaSuccess ? LADLASSO_OK : LADLASSO_ERR_CUDA;
+  return launch_fit_block(a, st, sms, G, d->fits_per_block) == cudaSuccess ? LADLASSO_OK
+                                                                          : LADLASSO_ERR_CUDA;
 }

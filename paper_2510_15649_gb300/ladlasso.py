@@ -31,7 +31,7 @@ class Opts(C.Structure):
                 ("chop_max_probes", C.c_int32), ("chop_max_extend", C.c_int32),
                 ("probe_max_sweeps", C.c_int32), ("polish", C.c_int32),
                 ("max_pivots", C.c_int32), ("tol_opt", C.c_float),
-                ("lambda_min_floor", C.c_float)]
+                ("lambda_min_floor", C.c_float), ("chop_sections", C.c_int32)]
 
 
 class Dims(C.Structure):
@@ -39,7 +39,8 @@ class Dims(C.Structure):
                 ("ldX", C.c_int64), ("rows_X", C.c_int64), ("total_rows", C.c_int64),
                 ("p", C.c_void_p), ("n_rows", C.c_void_p), ("b_init", C.c_void_p), ("fit_status", C.c_void_p),
                 ("basis_out", C.c_void_p), ("counters", C.c_void_p), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t), ("opts", C.c_void_p)]
+                ("workspace_bytes", C.c_size_t), ("opts", C.c_void_p),
+                ("group_threads", C.c_int32), ("fits_per_block", C.c_int32)]
 
 
 class LadLassoError(RuntimeError):
@@ -48,7 +49,8 @@ class LadLassoError(RuntimeError):
 
 SYMBOLS = ["ladlasso_default_opts", "ladlasso_workspace_size", "ladlasso_lambda_max",
            "ladlasso_lambda_path", "ladlasso_fit_batched", "ladlasso_fit_batched_thread",
-           "ladlasso_fit_backward", "ladlasso_status_string", "ladlasso_fit_batched_noalloc"]
+           "ladlasso_fit_backward", "ladlasso_status_string", "ladlasso_fit_batched_noalloc",
+           "ladlasso_launch_shape", "ladlasso_path_loss"]
 
 
 def lib():
@@ -77,6 +79,10 @@ def lib():
     L.ladlasso_fit_backward.argtypes = [P, P, P, P, DP, I32, P, P, P, I64, P, P, P, I64, P,
                                         P, P, P, P, P, P, P, P]
     L.ladlasso_fit_backward.restype = C.c_int
+    L.ladlasso_path_loss.argtypes = [P, P, P, P, DP, P, P, P]
+    L.ladlasso_path_loss.restype = C.c_int
+    L.ladlasso_launch_shape.argtypes = [DP, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]
+    L.ladlasso_launch_shape.restype = C.c_int
     L.ladlasso_status_string.argtypes = [C.c_int]
     L.ladlasso_status_string.restype = C.c_char_p
     _lib = L
@@ -184,10 +190,33 @@ def lambda_path(lmax: torch.Tensor, L: int, ratio: float = 1e-3, stream=None) ->
     return out
 
 
+@dataclass(frozen=True)
+class Launch:
+    """Launch shape of the batched fit (ladlasso_dims.group_threads and
+    .fits_per_block; zeros = the library's automatic choice)."""
+    group_threads: int = 0
+    fits_per_block: int = 0
+
+
+def launch_shape(pr: Problems, launch: Launch | None = None) -> tuple:
+    """(threads per fit, fits per block, max rows) the library would use."""
+    d = Dims()
+    d.P_cols, d.n_max = pr.P, pr.n_max
+    if launch is not None:
+        d.group_threads, d.fits_per_block = launch.group_threads, launch.fits_per_block
+    g, f, m = C.c_int32(), C.c_int32(), C.c_int32()
+    rc = lib().ladlasso_launch_shape(C.byref(d), C.byref(g), C.byref(f), C.byref(m))
+    if rc not in (OK, ERR_NOMEM):
+        _check(rc)
+    return g.value, f.value, m.value
+
+
 def fit(pr: Problems, lambdas: torch.Tensor, *, b_init=None, opts: Opts | None = None,
         basis: bool = False, counters: bool = False, per_thread: bool = False,
-        ws: torch.Tensor | None = None, out: dict | None = None, stream=None) -> dict:
+        ws: torch.Tensor | None = None, out: dict | None = None, stream=None,
+        launch: Launch | None = None) -> dict:
     """Fit every problem along its lambda path.  lambdas: [B, L] float32 (device).
+    `launch` overrides the launch shape (see tune.autotune).
     Returns dict(b [B,L,P], obj [B,L], status [B,L], basis?, counters?)."""
     B, P = pr.B, pr.P
     lam = lambdas.reshape(B, -1)
@@ -204,9 +233,24 @@ def fit(pr: Problems, lambdas: torch.Tensor, *, b_init=None, opts: Opts | None =
             out["counters"] = torch.empty((B, L, 8), dtype=torch.int32, device=dev)
     d = pr.dims(L, ws, opts, b_init=b_init, status=out["status"], basis=out.get("basis"),
                 counters=out.get("counters"))
+    if launch is not None:
+        d.group_threads, d.fits_per_block = launch.group_threads, launch.fits_per_block
     fn = lib().ladlasso_fit_batched_thread if per_thread else lib().ladlasso_fit_batched
     _check(fn(_ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), _ptr(lam.contiguous()),
               _ptr(out["b"]), _ptr(out["obj"]), C.byref(d), _stream(stream)))
+    return out
+
+
+def path_loss(val: Problems, b: torch.Tensor, stream=None) -> torch.Tensor:
+    """sum_v |y_v - x_v . b[q, l]| over the rows of problem q of `val`, for
+    every path position l of b [B, L, P] (device).  Returns [B, L]."""
+    B = val.B
+    L = int(b.shape[1])
+    out = torch.empty((B, L), dtype=torch.float32, device=val.X.device)
+    d = val.dims(L, out)
+    d.workspace, d.workspace_bytes = None, 0
+    _check(lib().ladlasso_path_loss(_ptr(val.X), _ptr(val.y), _ptr(val.row_idx), _ptr(val.offsets),
+                                    C.byref(d), _ptr(b.contiguous()), _ptr(out), _stream(stream)))
     return out
 
 

@@ -1,0 +1,88 @@
+"""Autotuner for the batched fit's launch shape.
+
+The fit kernel has two shapes (one warp per fit with several fits per
+thread block, or one 512-thread block per fit) and, for the one-warp shape,
+a number of fits per block bounded by shared memory.  More fits per block
+hide more latency but also keep more gathered designs live in L2 at once,
+so the best count depends on the problem mix.  `autotune` times every
+candidate on an evenly strided sample of the problem set (same size mix)
+with CUDA events and returns the fastest; choices are cached per device and
+problem-set signature.  Per-fit results do not depend on fits_per_block;
+the two shapes agree within the float32 tolerance.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import ladlasso as ll
+
+_cache: dict = {}
+
+
+def candidates(pr: ll.Problems) -> list:
+    """Launch shapes the library accepts for `pr`."""
+    out = []
+    g, fmax, mrows = ll.launch_shape(pr, ll.Launch(32, 0))
+    if pr.n_max <= mrows:
+        lo = max(1, fmax // 2)
+        out += [ll.Launch(32, f) for f in range(fmax, lo - 1, -1)]
+    g, _, mrows = ll.launch_shape(pr, ll.Launch(512, 0))
+    if pr.n_max <= mrows:
+        out.append(ll.Launch(512, 0))
+    return out
+
+
+def _subset(pr: ll.Problems, lambdas: torch.Tensor, every: int):
+    """Every `every`-th problem of pr as its own problem set (device copies)."""
+    off = pr.offsets.cpu().numpy()
+    qs = np.arange(0, pr.B, every)
+    lens = off[qs + 1] - off[qs]
+    idx = np.concatenate([np.arange(off[q], off[q + 1]) for q in qs]) if len(qs) else np.zeros(0, np.int64)
+    dev = pr.X.device
+    idx_t = torch.as_tensor(idx, device=dev)
+    qs_t = torch.as_tensor(qs, device=dev)
+    new_off = torch.as_tensor(np.concatenate([[0], np.cumsum(lens)]).astype(np.int64), device=dev)
+    y = pr.y[idx_t]
+    if pr.row_idx is None:
+        X, row_idx = pr.X[idx_t], None
+    else:
+        X, row_idx = pr.X, pr.row_idx[idx_t]
+    sub = ll.Problems(X=X, y=y, offsets=new_off, row_idx=row_idx,
+                      p=None if pr.p is None else pr.p[qs_t], P=pr.P, n_max=pr.n_max,
+                      n_rows=None if pr.n_rows is None else pr.n_rows[qs_t])
+    return sub, lambdas.reshape(pr.B, -1)[qs_t].contiguous()
+
+
+def autotune(pr: ll.Problems, lambdas: torch.Tensor, *, opts: ll.Opts | None = None,
+             sample_problems: int = 512, repeats: int = 2, use_cache: bool = True) -> tuple:
+    """Fastest launch shape for fitting `pr` along `lambdas`.
+    Returns (Launch, {shape: seconds})."""
+    L = int(lambdas.reshape(pr.B, -1).shape[1])
+    dev = pr.X.device
+    key = (torch.cuda.get_device_name(dev), pr.P, pr.n_max, pr.B, L, pr.row_idx is None)
+    if use_cache and key in _cache:
+        return _cache[key]
+    cands = candidates(pr)
+    if not cands:
+        raise ll.LadLassoError("no launch shape holds problems of n_max rows")
+    every = max(1, pr.B // max(1, sample_problems))
+    sub, lam = _subset(pr, lambdas, every) if every > 1 else (pr, lambdas)
+    ws = ll.workspace(sub, L)
+    stream = torch.cuda.current_stream(dev)
+    times = {}
+    for c in cands:
+        ll.fit(sub, lam, ws=ws, opts=opts, launch=c)  # warm-up
+        best = float("inf")
+        for _ in range(repeats):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ll.fit(sub, lam, ws=ws, opts=opts, launch=c)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        times[c] = best
+    choice = min(times, key=times.get)
+    _cache[key] = (choice, times)
+    return choice, times

@@ -8,10 +8,13 @@ same float32 lambdas, converted to float64.
 
 "Unique" means the oracle's certificate shows a strict vertex whose
 complementarity margin (1 - max|u_E|, 1 - max_off |X^T u|/lambda) is at
-least MARGIN.  Below that the optimum is degenerate to within float32
-resolution (e.g. lambda within rounding of lambda_max): several vertices
-reach F* to within 1e-5, so only the objective -- the one unique quantity --
-is compared there."""
+least MARGIN, and whose support is the same at lambda * (1 -+ LAM_REL).
+Otherwise the optimum is degenerate to within float32 resolution: several
+vertices reach F* to within 1e-5, or a breakpoint of the solution path
+lies within float32 rounding of lambda (e.g. lambda rounded a few ulp
+below lambda_max, where the FP64 optimum carries a coefficient of order
+(lambda_max - lambda) / lambda), so only the objective -- the one unique
+quantity -- is compared there."""
 import numpy as np
 
 import oracle
@@ -19,6 +22,7 @@ import oracle
 REL_OBJ = 1e-5
 REL_COEF = 1e-4
 MARGIN = 1e-4
+LAM_REL = 2e-6  # float32 multiplier sums over 1e4 rows carry ~1e-6 relative error
 
 
 def compare(batch, lam, b_gpu, obj_gpu, status_gpu, problems=None, opts=None):
@@ -53,6 +57,12 @@ def compare(batch, lam, b_gpu, obj_gpu, status_gpu, problems=None, opts=None):
                 _, info = oracle.certify(X, y, ref["b"][l], lam[q, l])
                 margin = min(1.0 - info["u_e_max"], 1.0 - info["c_off_max"])
                 unique = info["unique"] and margin >= MARGIN
+            if unique:
+                sup = ref["b"][l] != 0
+                for sg in (-1.0, 1.0):
+                    alt = oracle.fit_path(X, y, [lam[q, l] * (1.0 + sg * LAM_REL)],
+                                          b_init=ref["b"][l], opts=opts)
+                    unique = unique and np.array_equal(alt["b"][0] != 0, sup)
             if unique:
                 if not np.array_equal(bg != 0, ref["b"][l] != 0):
                     bad.append((q, l, "support"))

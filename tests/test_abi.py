@@ -37,3 +37,31 @@ def test_host_only_entry_points():
     # invalid host arguments are rejected before any CUDA call
     assert L.ladlasso_lambda_path(None, -1, 1, 0.5, None, None) == ladlasso.ERR_INVALID
     assert L.ladlasso_fit_batched(None, None, None, None, None, None, None, None, None) == ladlasso.ERR_INVALID
+
+
+def test_launch_shape_is_host_only_and_consistent():
+    from paper_2510_15649_gb300 import ladlasso as ll
+
+    class Pr:  # the two fields launch_shape reads
+        def __init__(self, P, n_max):
+            self.P, self.n_max = P, n_max
+
+    g, f, m = ll.launch_shape(Pr(32, 2000))
+    assert g == 32 and 1 <= f <= 16 and m >= 8192
+    # fewer rows per fit -> at least as many fits per block
+    g2, f2, _ = ll.launch_shape(Pr(32, 500))
+    assert g2 == 32 and f2 >= f
+    # the hint caps the count and never raises it
+    assert ll.launch_shape(Pr(32, 2000), ll.Launch(32, 3))[1] == min(3, f)
+    assert ll.launch_shape(Pr(32, 2000), ll.Launch(32, 99))[1] == f
+    # beyond 8192 rows: one block per fit, up to the shared-memory row limit
+    g3, f3, m3 = ll.launch_shape(Pr(128, 20000))
+    assert g3 == 512 and f3 == 1 and m3 >= 20000
+    assert ll.launch_shape(Pr(32, 2000), ll.Launch(512, 0))[0] == 512
+    # n_max beyond the one-warp limit with an explicit one-warp request
+    g4, f4, m4 = ll.launch_shape(Pr(32, 50000), ll.Launch(32, 0))
+    assert g4 == 32 and m4 < 50000
+    # invalid shapes
+    import pytest
+    with pytest.raises(ll.LadLassoError):
+        ll.launch_shape(Pr(32, 2000), ll.Launch(64, 0))

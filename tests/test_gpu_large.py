@@ -1,0 +1,138 @@
+"""Parity of the block-per-fit path (one CTA per fit, columns streamed from
+global memory), used when a problem set holds problems too long for the
+one-warp path.  Small problems are forced onto it through n_max; long
+problems and the 256 x 20000 x 128 workload are checked by the oracle's
+certificate on sampled fits."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_15649_gb300 import synth
+
+from gpu_common import compare
+
+pytestmark = pytest.mark.gpu
+
+BLOCK_N_MAX = 9000  # above the one-warp path's row limit
+
+
+@pytest.fixture(scope="module")
+def ll():
+    import torch  # noqa: F401
+    from paper_2510_15649_gb300 import build
+    build.build()
+    from paper_2510_15649_gb300 import ladlasso
+    return ladlasso
+
+
+def _run(ll, batch, lam_np, n_max=None, **kw):
+    import torch
+    pr = ll.Problems.from_numpy(batch)
+    if n_max is not None:
+        pr.n_max = n_max
+    lam = torch.as_tensor(np.asarray(lam_np, np.float32), device="cuda")
+    out = ll.fit(pr, lam, basis=True, counters=True, **kw)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _oracle_lams(batch, L, ratio):
+    B = len(batch["p"])
+    lm = np.array([oracle.lambda_max(*oracle.problem(batch, q)) for q in range(B)])
+    return (lm[:, None] * ratio ** (np.arange(L) / max(L - 1, 1))[None, :]).astype(np.float32)
+
+
+def test_block_path_small_problems_parity(ll):
+    # ragged n (several row batches of 8 warps x 256 rows and a tail), p 1..12
+    batch = synth.batched_like(24, 20, 2600, 1, 12, R=3000, P=12, seed=31)
+    lam = _oracle_lams(batch, 4, 1e-3)
+    out = _run(ll, batch, lam, n_max=BLOCK_N_MAX)
+    res = compare(batch, lam, out["b"], out["obj"], out["status"])
+    assert not res["bad"], res["bad"][:10]
+    assert np.all((out["status"] & 1) == 0)
+
+
+def test_block_path_alone_and_in_a_batch(ll):
+    batch = synth.batched_like(10, 30, 900, 2, 8, R=1000, P=8, seed=33)
+    lam = _oracle_lams(batch, 3, 1e-2)
+    full = _run(ll, batch, lam, n_max=BLOCK_N_MAX)
+    for q in [0, 9]:
+        o0, o1 = batch["offsets"][q], batch["offsets"][q + 1]
+        one = dict(X=batch["X"], y=batch["y"][o0:o1], row_idx=batch["row_idx"][o0:o1],
+                   offsets=np.array([0, o1 - o0], np.int64), p=batch["p"][q:q + 1])
+        alone = _run(ll, one, lam[q:q + 1], n_max=BLOCK_N_MAX)
+        np.testing.assert_array_equal(alone["b"][0], full["b"][q])
+        np.testing.assert_array_equal(alone["obj"][0], full["obj"][q])
+
+
+def test_block_path_long_problems_parity(ll):
+    # real long problems (n up to 12000): oracle path on each
+    batch = synth.batched_like(3, 9000, 12000, 6, 16, R=12000, P=16, seed=35)
+    lam = _oracle_lams(batch, 3, 1e-2)
+    out = _run(ll, batch, lam)
+    res = compare(batch, lam, out["b"], out["obj"], out["status"])
+    assert not res["bad"], res["bad"][:10]
+
+
+def test_block_path_edge_cases(ll):
+    # empty problem, p = 1, NaN / negative lambdas, on the block path
+    X = np.random.default_rng(0).standard_normal((50, 3)).astype(np.float32)
+    y = (X @ np.array([1.0, -2, 0]) + 0.1).astype(np.float32)
+    batch = dict(X=X, y=y[:45], row_idx=np.arange(45, dtype=np.int32),
+                 offsets=np.array([0, 0, 20, 45], np.int64), p=np.array([3, 1, 3], np.int32))
+    lam = np.array([[1.0, 0.5], [1.0, np.nan], [-1.0, 0.1]], np.float32)
+    out = _run(ll, batch, lam, n_max=BLOCK_N_MAX)
+    assert np.all(out["b"][0] == 0) and np.all(out["status"][0] == 0)
+    assert out["status"][1, 1] == 2 and out["status"][2, 0] == 2
+    res = compare(batch, lam, out["b"], out["obj"], out["status"], problems=[1])
+    assert not [b for b in res["bad"] if b[1] == 0], res["bad"]
+
+
+def _vertex(X, y, codes):
+    """FP64 vertex of the basis the kernel reports: rows i (code >= 0) on
+    their hyperplanes x_i . b = y_i, coordinates j (code -(j+1)) at 0."""
+    p = X.shape[1]
+    A = np.zeros((p, p))
+    r = np.zeros(p)
+    for k, cd in enumerate(codes):
+        if cd >= 0:
+            A[k], r[k] = X[cd], y[cd]
+        else:
+            A[k, -cd - 1] = 1.0
+    return np.linalg.solve(A, r)
+
+
+def test_large_workload_sampled_certificates(ll):
+    """256 problems x 20000 rows x 128 columns, 32-lambda path, in one
+    launch; on sampled fits the FP64 vertex of the reported basis carries a
+    zero duality gap (the oracle's certificate) and the kernel's b is within
+    the objective tolerance of it."""
+    import torch
+    big = synth.large()
+    pr = ll.Problems.from_numpy(big)
+    lm = ll.lambda_max(pr)
+    lam = ll.lambda_path(lm, 32, 1e-3)
+    out = ll.fit(pr, lam, basis=True)
+    torch.cuda.synchronize()
+    st = out["status"].cpu().numpy()
+    b = out["b"].cpu().numpy().astype(np.float64)
+    obj = out["obj"].cpu().numpy().astype(np.float64)
+    basis = out["basis"].cpu().numpy()
+    lam_h = lam.cpu().numpy().astype(np.float64)
+    assert np.all((st & 2) == 0)
+    assert np.mean((st & 1) == 0) >= 0.99
+    rng = np.random.default_rng(7)
+    n = 20000
+    for q in rng.choice(256, 3, replace=False):
+        Xq = big["X"][q * n:(q + 1) * n].astype(np.float64)
+        yq = big["y"][q * n:(q + 1) * n].astype(np.float64)
+        for l in (0, 15, 31):
+            if st[q, l] & 1:
+                continue
+            bv = _vertex(Xq, yq, basis[q, l])
+            Fv = oracle.objective(Xq, yq, bv, lam_h[q, l])
+            gap, _ = oracle.certify(Xq, yq, bv, lam_h[q, l])
+            assert gap <= 1e-7 * max(1.0, Fv), (q, l, gap, Fv)
+            Fg = oracle.objective(Xq, yq, b[q, l], lam_h[q, l])
+            assert abs(Fg - Fv) <= 1e-5 * max(1.0, Fv), (q, l, Fg, Fv)
+            assert abs(obj[q, l] - Fg) <= 1e-5 * max(1.0, Fg)

@@ -149,3 +149,18 @@ def test_invalid_arguments_return_errors(ll):
     d.P_cols = 0
     assert L.ladlasso_fit_batched(p, p, None, C.c_void_p(off.data_ptr()), p, p, p, C.byref(d), s) == ll.ERR_INVALID
     assert L.ladlasso_lambda_path(p, 1, 1, 2.0, p, s) == ll.ERR_INVALID
+
+
+@pytest.mark.parametrize("per_thread", [False, True])
+def test_four_section_chop_parity(ll, per_thread):
+    # the "quadrature" reading of the chop (three inner probes per step)
+    batch = synth.batched_like(32, 20, 600, 2, 10, R=700, P=10, seed=13)
+    lam = _oracle_lams(batch, 4, 1e-3)
+    out = _run(ll, batch, lam, per_thread, opts=ll.default_opts(chop_sections=4))
+    res = compare(batch, lam, out["b"], out["obj"], out["status"],
+                  opts=oracle.default_opts(chop_sections=4))
+    assert not res["bad"], res["bad"][:10]
+    # the chop ran and probed in threes
+    c = out["counters"]
+    ran = (c[..., 3] & 2) != 0
+    assert ran.any()

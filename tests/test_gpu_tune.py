@@ -1,0 +1,68 @@
+"""Launch shapes and the autotuner: results do not depend on the number of
+fits per block; the block-per-fit shape agrees with the one-warp shape
+within the parity tolerance; the autotuner returns one of the candidates."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_15649_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ll():
+    import torch  # noqa: F401
+    from paper_2510_15649_gb300 import build
+    build.build()
+    from paper_2510_15649_gb300 import ladlasso
+    return ladlasso
+
+
+def _setup(ll):
+    import torch
+    batch = synth.batched_like(96, 30, 900, 2, 16, R=1000, P=16, seed=41)
+    pr = ll.Problems.from_numpy(batch)
+    lam = ll.lambda_path(ll.lambda_max(pr), 4, 1e-2)
+    torch.cuda.synchronize()
+    return batch, pr, lam
+
+
+def test_results_do_not_depend_on_fits_per_block(ll):
+    import torch
+    batch, pr, lam = _setup(ll)
+    ref = ll.fit(pr, lam)
+    for f in (1, 3):
+        out = ll.fit(pr, lam, launch=ll.Launch(32, f))
+        torch.cuda.synchronize()
+        assert torch.equal(out["b"], ref["b"]) and torch.equal(out["obj"], ref["obj"])
+        assert torch.equal(out["status"], ref["status"])
+
+
+def test_block_shape_agrees_with_warp_shape(ll):
+    import torch
+    batch, pr, lam = _setup(ll)
+    a = ll.fit(pr, lam, launch=ll.Launch(32, 0))
+    b = ll.fit(pr, lam, launch=ll.Launch(512, 0))
+    torch.cuda.synchronize()
+    lh = lam.cpu().numpy().astype(np.float64)
+    ba, bb = a["b"].cpu().numpy(), b["b"].cpu().numpy()
+    for q in range(0, 96, 7):
+        X, y = oracle.problem(batch, q)
+        p = X.shape[1]
+        for l in range(4):
+            fa = oracle.objective(X, y, ba[q, l, :p].astype(np.float64), lh[q, l])
+            fb = oracle.objective(X, y, bb[q, l, :p].astype(np.float64), lh[q, l])
+            assert abs(fa - fb) <= 1e-5 * max(1.0, fa), (q, l, fa, fb)
+
+
+def test_autotune_picks_a_candidate_and_caches(ll):
+    from paper_2510_15649_gb300 import tune
+    batch, pr, lam = _setup(ll)
+    cands = tune.candidates(pr)
+    assert ll.Launch(512, 0) in cands and any(c.group_threads == 32 for c in cands)
+    choice, times = tune.autotune(pr, lam, sample_problems=32)
+    assert choice in cands and set(times) == set(cands)
+    assert all(t > 0 for t in times.values())
+    again, _ = tune.autotune(pr, lam, sample_problems=32)
+    assert again == choice

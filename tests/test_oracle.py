@@ -294,6 +294,28 @@ def test_chop_only_variant_is_not_always_optimal_but_never_worse():
         assert r["f"][0] <= F(X, y, bc, lam) * (1 + 1e-12)
 
 
+@pytest.mark.parametrize("sections", [3, 4])
+def test_chop_is_exact_on_two_coordinates(sections):
+    # p = 2: a probe's restricted descent is an exact 1-D minimisation over
+    # the other coordinate, so g(t) is the convex partial minimum and both
+    # the ternary chop (3 sections) and the four-section "quadrature"
+    # reading close in on the global minimum (Sections 3.4-3.5); no polish.
+    rng = np.random.default_rng(47)
+    ran = 0
+    for trial in range(12):
+        X = rng.standard_normal((30, 2))
+        X[:, 1] = 0.9 * X[:, 0] + 0.3 * X[:, 1]  # correlated axes stall CCD
+        y = X @ np.array([1.5, -2.0]) + rng.laplace(0, 0.5, 30)
+        lam = 0.05 * oracle.lambda_max(X, y)
+        fb, _, _ = oracle.brute_force(X, y, lam)
+        o = oracle.default_opts(polish=0, chop_sections=sections, chop_tol=1e-13,
+                                chop_max_probes=400, chop_max_extend=80)
+        r = oracle.fit_path(X, y, [lam], opts=o)
+        ran += r["stats"][0]["chop_ran"]
+        assert rel(r["f"][0], fb) < 1e-9, (trial, r["f"][0], fb)
+    assert ran >= 2
+
+
 # ---------------------------------------------------------------- gradient
 
 def test_active_set_gradient_matches_finite_differences():
