@@ -12,8 +12,10 @@ instead (bounded samples of the same workload on the host cores).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -45,6 +47,10 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-seconds", type=float, default=0.25,
                     help="length of the Poisson arrival trace (20k requests/s)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 20000 x 128 block-per-fit measurement")
+    ap.add_argument("--large-problems", type=int, default=256)
+    ap.add_argument("--no-tune", action="store_true", help="library's default launch shape")
     return ap.parse_args()
 
 
@@ -156,6 +162,22 @@ def log(*a):
     print("[bench]", *a, file=sys.stderr, flush=True)
 
 
+def profile_traffic(name: str, source: str):
+    """DRAM bytes per launch recorded in profiles/<name> by an ncu capture,
+    if it was taken on the current source of the kernel (its SHA-256 is
+    recorded beside the number); None otherwise."""
+    try:
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+        cur = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
+    if not m or not h or h.group(1) != cur:
+        return None
+    return float(m.group(1))
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -188,10 +210,20 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    # launch shape: autotuned on every 2nd problem (outside the timed region)
+    launch, tuned = None, {}
+    if not args.no_tune:
+        from paper_2510_15649_gb300 import tune
+        lam0 = ll.lambda_path(ll.lambda_max(pr, ws), L, 1e-3)
+        # the sample must outnumber the resident fits (~1000) so that it
+        # measures throughput, not the longest single fit
+        launch, tuned = tune.autotune(pr, lam0, sample_problems=max(1, B // 2))
+        log(f"autotune {launch} {tuned}")
+
     def step():
         lm = ll.lambda_max(pr, ws)
         lam = ll.lambda_path(lm, L, 1e-3)
-        ll.fit(pr, lam, ws=ws, out=out)
+        ll.fit(pr, lam, ws=ws, out=out, launch=launch)
         return lam
 
     launches_per_step = 5  # 2 offset checks, lambda_max, lambda_path, fit
@@ -235,7 +267,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ll.fit(pr, lam_fixed, ws=ws, out=out)
+        ll.fit(pr, lam_fixed, ws=ws, out=out, launch=launch)
         e1.record(stream)
         torch.cuda.synchronize()
         kt.append(e0.elapsed_time(e1) / 1e3)
@@ -266,7 +298,7 @@ def main():
                          P=pr.P, n_max=pr.n_max)
         lm = ll.lambda_max(p2, ws)
         lam2 = ll.lambda_path(lm, L, 1e-3)
-        o2 = ll.fit(p2, lam2, ws=ws)
+        o2 = ll.fit(p2, lam2, ws=ws, launch=launch)
         hb.copy_(o2["b"], non_blocking=True)
         hobj.copy_(o2["obj"], non_blocking=True)
         hst.copy_(o2["status"], non_blocking=True)
@@ -281,7 +313,13 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "problems_per_gpu": B, "lambdas": L,
-                       "fits_per_gpu": fits, "l2": "flushed between timed steps (256 MB write)"},
+                       "fits_per_gpu": fits, "l2": "flushed between timed steps (256 MB write)",
+                       "launch": None if launch is None else {
+                           "group_threads": launch.group_threads,
+                           "fits_per_block": launch.fits_per_block,
+                           "work_order": launch.work_order,
+                           "autotune_ms": {f"{c.group_threads}x{c.fits_per_block}/o{c.work_order}":
+                                           round(1e3 * t, 2) for c, t in tuned.items()}}},
             "certified_fraction": certified / fits,
             "gpu_launches": launches_per_step * args.steps,
             "e2e": {"value": certified * world / t_e2e, "unit": "fits/s",
@@ -317,10 +355,56 @@ def main():
     achieved = flops_per_ru * ru / t_fit / 1e12
     peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x clock
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None,
+                        "frac": achieved / peak,
+                        "traffic": profile_traffic("launches_batched4096.md",
+                                                   "paper_2510_15649_gb300/csrc/fit_block.cu"),
                         "kernel": "fit_block_kernel", "kernel_ms": 1e3 * t_fit,
                         "row_updates_per_launch": ru}
     line["clocks"] = clk_s
+
+    # long problems: 20000 x 128 per fit, one 512-thread block per fit,
+    # columns streamed from HBM (one launch, timed with events)
+    if not args.no_large and rank == 0:
+        try:
+            Bl = args.large_problems
+            big = synth.large(B=Bl)
+            pb = ll.Problems.from_numpy(big, device=dev)
+            del big
+            wsb = ll.workspace(pb, 32)
+            lamb = ll.lambda_path(ll.lambda_max(pb, wsb), 32, 1e-3)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ob = ll.fit(pb, lamb, ws=wsb, counters=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tl = e0.elapsed_time(e1) / 1e3
+            cb = ob["counters"].cpu().numpy().astype(np.float64)
+            sb = ob["status"].cpu().numpy()
+            n_l, p_l = 20000, 128
+            # algorithmic bytes: one read of a column (4n B) per selection
+            # pass, one read of the design (4np B) per polish pivot
+            byts = 4.0 * n_l * float(cb[..., 4].sum() + p_l * cb[..., 2].sum())
+            hbm_peak = 6701.5
+            try:
+                hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+            except (OSError, KeyError, ValueError):
+                pass
+            cert = int(np.sum((sb & 3) == 0))
+            line["large"] = {
+                "workload": f"{Bl} problems x 20000 rows x 128 columns, AR(1) 0.5, L=32",
+                "fits_per_s": cert / tl, "kernel_ms": 1e3 * tl, "certified_fraction": cert / sb.size,
+                "launch": "one 512-thread block per fit",
+                "roofline": {"bound": "hbm", "achieved": byts / tl / 1e9, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": byts / tl / 1e9 / hbm_peak,
+                             "bytes_per_launch": byts, "traffic": None},
+                "pivots_mean": float(cb[..., 2].mean()), "passes_mean": float(cb[..., 4].mean())}
+            log(f"large {line['large']}")
+            del pb, wsb, ob
+            torch.cuda.empty_cache()
+        except Exception as ex:
+            line["large"] = {"error": str(ex)}
 
     # thread-per-fit comparison: the paper's one-fit-per-thread layout is far
     # too slow for the full workload inside a bench run, so both kernels are

@@ -127,8 +127,13 @@ void ladlasso_default_opts(ladlasso_opts* o);
  *            float32 tolerance, not bit for bit
  * fits_per_block  one-warp shape: at most this many fits per thread block
  *            (0 = as many as shared memory holds, at most 16); results do
- *            not depend on it.  Both are chosen by the autotuner of the
- *            Python binding; zero-initialise them otherwise */
+ *            not depend on it.
+ * work_order order in which the fits take problems: 0 = longest first
+ *            (n * p), 1 = longest and shortest alternately (a smaller L2
+ *            working set of resident designs); any other value is
+ *            LADLASSO_ERR_INVALID.  Results do not depend on it.
+ *            The three are chosen by the autotuner of the Python binding;
+ *            zero-initialise them otherwise */
 typedef struct ladlasso_dims {
   int32_t B, P_cols, L;
   int32_t n_max;
@@ -144,6 +149,7 @@ typedef struct ladlasso_dims {
   const ladlasso_opts* opts;
   int32_t group_threads;
   int32_t fits_per_block;
+  int32_t work_order;
 } ladlasso_dims;
 
 /* Bytes of device workspace any entry point below needs for a problem set

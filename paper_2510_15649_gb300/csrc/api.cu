@@ -16,7 +16,7 @@ cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t total
                                     cudaStream_t st);
 cudaError_t launch_lambda_max(const FitArgs& a, float* lmax, cudaStream_t st, int num_sms);
 cudaError_t launch_order(const int64_t* offsets, const int32_t* nr, const int32_t* p, int P, int B,
-                         int* order, cudaStream_t st);
+                         int policy, int* order, cudaStream_t st);
 cudaError_t launch_lambda_path(const float* lmax, int B, int L, float ratio, float* lam,
                                cudaStream_t st);
 cudaError_t launch_path_loss(const float* X, int64_t ldX, int64_t rows_X, const float* y,
@@ -203,7 +203,8 @@ static int fit_common(const float* X, const float* y, const int32_t* row_idx,
   if (rc != LADLASSO_OK) return rc;
   if (!lambdas || !b_out || !obj_out) return LADLASSO_ERR_INVALID;
   const int G = ll::launch_group(dims);
-  if (G == 0 || dims->fits_per_block < 0) return LADLASSO_ERR_INVALID;
+  if (G == 0 || dims->fits_per_block < 0 || dims->work_order < 0 || dims->work_order > 1)
+    return LADLASSO_ERR_INVALID;
   if (!per_thread && dims->n_max > ll::fit_block_max_rows(G, dims->P_cols)) return LADLASSO_ERR_NOMEM;
   a.lambdas = lambdas;
   a.b_out = b_out;
@@ -214,7 +215,8 @@ static int fit_common(const float* X, const float* y, const int32_t* row_idx,
   if (rc != LADLASSO_OK) return rc;
   int sms = num_sms();
   if (sms <= 0) return LADLASSO_ERR_CUDA;
-  if (!per_thread && ll::launch_order(a.offsets, a.n_rows, a.p, a.P, a.B, a.order, st) != cudaSuccess)
+  if (!per_thread && ll::launch_order(a.offsets, a.n_rows, a.p, a.P, a.B, dims->work_order,
+                                      a.order, st) != cudaSuccess)
     return LADLASSO_ERR_CUDA;
   cudaError_t e = per_thread ? ll::launch_fit_thread(a, st, sms)
                              : ll::launch_fit_block(a, st, sms, G, dims->fits_per_block);

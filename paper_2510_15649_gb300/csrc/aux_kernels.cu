@@ -61,7 +61,10 @@ __global__ void lambda_max_kernel(FitArgs a, float* lmax) {
 // Work order for the persistent fit kernels: problems sorted by decreasing
 // estimated cost n * p (longest first keeps the tail short).  One block;
 // counting sort over logarithmic cost buckets (order within a bucket is
-// arbitrary and does not affect any result).
+// arbitrary and does not affect any result).  policy 1 interleaves the two
+// ends of that order (longest, shortest, second longest, ...): the fits
+// resident at one time then hold designs of mixed size, a smaller L2
+// working set than the largest-first wave.  No result depends on it.
 constexpr int kBuckets = 128;
 __device__ __forceinline__ int cost_bucket(const int64_t* offsets, const int32_t* nr,
                                            const int32_t* p, int P, int q) {
@@ -75,7 +78,7 @@ __device__ __forceinline__ int cost_bucket(const int64_t* offsets, const int32_t
 }
 
 __global__ void order_kernel(const int64_t* offsets, const int32_t* nr, const int32_t* p, int P,
-                             int B, int* order) {
+                             int B, int policy, int* order) {
   __shared__ int hist[kBuckets];
   for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) hist[b] = 0;
   __syncthreads();
@@ -88,6 +91,7 @@ __global__ void order_kernel(const int64_t* offsets, const int32_t* nr, const in
   __syncthreads();
   for (int q = threadIdx.x; q < B; q += blockDim.x) {
     int pos = atomicAdd(&hist[cost_bucket(offsets, nr, p, P, q)], 1);
+    if (policy == 1) pos = pos < (B + 1) / 2 ? 2 * pos : 2 * (B - 1 - pos) + 1;
     order[pos] = q;
   }
 }
@@ -173,9 +177,9 @@ cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t total
 }
 
 cudaError_t launch_order(const int64_t* offsets, const int32_t* nr, const int32_t* p, int P, int B,
-                         int* order, cudaStream_t st) {
+                         int policy, int* order, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
-  order_kernel<<<1, 1024, 0, st>>>(offsets, nr, p, P, B, order);
+  order_kernel<<<1, 1024, 0, st>>>(offsets, nr, p, P, B, policy, order);
   return cudaGetLastError();
 }
 

@@ -45,6 +45,8 @@ constexpr int kMaxPasses = 64; // cap on fused passes per 1-D step
 constexpr int kAxis = 0, kEdge = 1;
 constexpr int kSubCap = 128;   // block path: selection sub-buffer per warp
 constexpr int kBlockG = 512;   // block path: threads per fit
+constexpr int kHist = 32;               // polish: bases remembered for cycle detection
+constexpr float kStallTolFactor = 50.f; // cycling vertex accepted when violations are below this x tol
 // dynamic shared memory one block may take: 227 KB less the static state
 constexpr size_t kDynSmemLimit = 227 * 1024 - 8 * 1024;
 
@@ -53,11 +55,13 @@ struct St {
   float* rr;                           // residual [ncap]
   float* ck; float* cw; int* cid;      // selection buffer [cap]
   float* bv; float* bbest; float* dv; float* mu; float* tv; float* hv; float* dl;  // [P]
+  float* rv;                           // [P] refinement residual
   float* Bm;                           // [P*P]
   float* red2;                         // [W*P]
   int* code; int* phan; int* piv; int* perm; int* pcol;  // [P]
   int* code_prev; int* phan_prev;  // [P] last path position's final basis
   int* code_alt; int* phan_alt;    // [P] the other polish start
+  unsigned* bhist;                 // [kHist] hashes of the polish's recent bases
   float* sk; float* sw; int* sid;      // special breakpoints [P+1]
   unsigned* mask;                      // basis-row bitmap [maskw]
   float* redf; int* redi;              // reductions [W*16]
@@ -76,7 +80,8 @@ struct St {
   float lam, bj;
   // broadcast slots
   float lo, hi, acc, wpart, half, zstar, above;
-  int part, m, owner, q, flag, iter, first, has_prev;
+  int part, m, owner, q, flag, iter, first, has_prev, bland;
+  float worst;  // largest multiplier violation at the last test
   // fused-pass results
   float p_wl, p_wi, p_wt, p_amin;
   int p_cnt, p_ovf;
@@ -460,6 +465,12 @@ __device__ __forceinline__ void row_key(const St& s, int i, float& k, float& w) 
 // kBufCap keys inside go to the buffer (row order, then specials).  Rows
 // are taken kPassU per lane at a time so their loads overlap.
 constexpr int kPassU = 8;
+// rows per thread per batch in the whole-design loops (residual, edge
+// products, column sums), which read the gathered design straight from L2
+// or HBM: 16 loads in flight per thread.  The rows a thread visits, and
+// their order, do not depend on it.
+template <int G>
+constexpr int kRowU = 16;
 
 // The buffer pointers are passed in registers (restrict-qualified): going
 // through the shared state struct would reload them after every store.
@@ -1040,6 +1051,133 @@ __device__ __noinline__ void lu_solve_t(St& s, float* x) {
   __syncwarp();
 }
 
+// (one warp) one step of iterative refinement of x solving B x = h
+// (trans = false) or B^T x = h (trans = true) with the FP32 factors in Bm:
+// the residual is formed in FP64 from the basis normals (rows of X and unit
+// vectors, exact in FP32), the correction solved with the factors.  At
+// p = 128 the FP32 solve alone leaves multiplier errors of the order of the
+// optimality tolerance.
+__device__ __noinline__ void refine(St& s, float* x, const float* h, bool trans) {
+  const int lane = lane_id(), p = s.p;
+  for (int e = lane; e < p; e += 32) {
+    double acc = 0.0;
+    if (!trans) {  // e: basis position
+      const int cd = s.code[e];
+      if (cd >= 0)
+        for (int c = 0; c < p; ++c) acc += (double)xval(s, c, cd) * (double)x[c];
+      else
+        acc = (double)x[-cd - 1];
+    } else {       // e: column
+      for (int k = 0; k < p; ++k) {
+        const int cd = s.code[k];
+        const float nv = cd >= 0 ? xval(s, e, cd) : (e == -cd - 1 ? 1.f : 0.f);
+        acc += (double)nv * (double)x[k];
+      }
+    }
+    s.rv[e] = (float)((double)h[e] - acc);
+  }
+  __syncwarp();
+  if (trans) lu_solve_t(s, s.rv);
+  else lu_solve(s, s.rv);
+  for (int e = lane; e < p; e += 32) x[e] += s.rv[e];
+  __syncwarp();
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// (all G threads) LU with partial pivoting of Bm in place, the row
+// operations of each elimination step spread over the block; the pivot
+// choice is the one-warp routine's (largest |entry|, lowest row on ties).
+template <int G>
+__device__ __noinline__ bool lu_blk(St& s) {
+  const int tid = gtid<G>(), lane = lane_id(), warp = gwarp<G>(), p = s.p;
+  float* B = s.Bm;
+  for (int c = tid; c < p; c += G) s.perm[c] = c;
+  float am = 0.f;
+  for (int e = tid; e < p * p; e += G) am = fmaxf(am, fabsf(B[e]));
+  {
+    float f[1] = {0.f}, m[1] = {-am};
+    int si[1] = {0}, mi[1] = {0};
+    reduce<G, 1, 1, 1, 1>(s, f, m, si, mi);
+    am = -m[0];
+  }
+  for (int k = 0; k < p; ++k) {
+    if (warp == 0) {
+      float bvv = -1.f;
+      int bi = k;
+      for (int i = k + lane; i < p; i += 32)
+        if (fabsf(B[i * p + k]) > bvv) { bvv = fabsf(B[i * p + k]); bi = i; }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        float ov = __shfl_xor_sync(0xffffffffu, bvv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bvv || (ov == bvv && oi < bi)) { bvv = ov; bi = oi; }
+      }
+      if (lane == 0) { s.m = bi; s.flag = bvv > 1e-7f * am; }
+    }
+    __syncthreads();
+    if (!s.flag) return false;  // uniform
+    const int bi = s.m;
+    if (bi != k) {
+      for (int c = tid; c < p; c += G) {
+        float t = B[k * p + c]; B[k * p + c] = B[bi * p + c]; B[bi * p + c] = t;
+      }
+      if (tid == 0) { int t = s.perm[k]; s.perm[k] = s.perm[bi]; s.perm[bi] = t; }
+    }
+    __syncthreads();
+    const float pv = B[k * p + k];
+    for (int i = k + 1 + tid; i < p; i += G) B[i * p + k] /= pv;
+    __syncthreads();
+    const int rem = p - k - 1;
+    for (int e = tid; e < rem * rem; e += G) {
+      const int i = k + 1 + e / rem, c = k + 1 + e % rem;
+      B[i * p + c] -= B[i * p + k] * B[k * p + c];
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// (all G threads) the refinement of `refine` with the FP64 residual
+// spread over the warps (one basis position or column per warp, lanes over
+// the inner index); warp 0 solves for the correction.
+template <int G>
+__device__ __noinline__ void refine_blk(St& s, float* x, const float* h, bool trans) {
+  constexpr int W = G / 32;
+  const int lane = lane_id(), warp = gwarp<G>(), p = s.p;
+  __syncthreads();
+  for (int e = warp; e < p; e += W) {
+    double acc = 0.0;
+    if (!trans) {
+      const int cd = s.code[e];
+      if (cd >= 0) {
+        for (int c = lane; c < p; c += 32) acc += (double)xval(s, c, cd) * (double)x[c];
+      } else if (lane == 0) {
+        acc = (double)x[-cd - 1];
+      }
+    } else {
+      for (int k = lane; k < p; k += 32) {
+        const int cd = s.code[k];
+        const float nv = cd >= 0 ? xval(s, e, cd) : (e == -cd - 1 ? 1.f : 0.f);
+        acc += (double)nv * (double)x[k];
+      }
+    }
+    acc = warp_sum_d(acc);
+    if (lane == 0) s.rv[e] = (float)((double)h[e] - acc);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    if (trans) lu_solve_t(s, s.rv);
+    else lu_solve(s, s.rv);
+    for (int e = lane; e < p; e += 32) x[e] += s.rv[e];
+  }
+  __syncthreads();
+}
+
 // (one warp) form the basis matrix, factor it and snap b onto the basis
 // hyperplanes (phantom coordinates keep their value).  Sets s.flag.
 __device__ __noinline__ void snap(St& s) {
@@ -1068,10 +1206,13 @@ __device__ __noinline__ void snap(St& s) {
     s.hv[k] = cd >= 0 ? s.yq[cd] : (s.phan[k] ? s.bv[-cd - 1] : 0.f);
   }
   __syncwarp();
+  for (int k = lane; k < p; k += 32) s.mu[k] = s.hv[k];  // right-hand side (mu is free here)
+  __syncwarp();
   bool ok = lu(s);
   if (lane == 0) s.flag = ok;
   if (ok) {
     lu_solve(s, s.hv);
+    refine(s, s.hv, s.mu, false);
     for (int c = lane; c < p; c += 32) s.bv[c] = s.hv[c];
     __syncwarp();
     for (int k = lane; k < p; k += 32)
@@ -1080,10 +1221,44 @@ __device__ __noinline__ void snap(St& s) {
   __syncwarp();
 }
 
-// (one warp) multipliers from the column sums in red2, pick the most
-// violated basis hyperplane, and (if stepping) the edge direction dv.
+// (all G threads) snap: the one-warp routine for a warp; for a block the
+// basis matrix is formed, factored and refined by all warps.
 template <int G>
-__device__ __noinline__ void multipliers(St& s, bool step) {
+__device__ __noinline__ void snap_g(St& s) {
+  if (G == 32) {
+    snap(s);
+    return;
+  }
+  const int tid = gtid<G>(), warp = gwarp<G>(), p = s.p, pp = p * p;
+  for (int e = tid; e < pp; e += G) {
+    const int k = e / p, c = e - k * p, cd = s.code[k];
+    s.Bm[e] = cd >= 0 ? xval(s, c, cd) : (c == -cd - 1 ? 1.f : 0.f);
+  }
+  for (int k = tid; k < p; k += G) {
+    const int cd = s.code[k];
+    const float h = cd >= 0 ? s.yq[cd] : (s.phan[k] ? s.bv[-cd - 1] : 0.f);
+    s.hv[k] = h;
+    s.mu[k] = h;  // right-hand side (mu is free here)
+  }
+  __syncthreads();
+  const bool ok = lu_blk<G>(s);  // group-uniform
+  if (ok) {
+    if (warp == 0) lu_solve(s, s.hv);
+    refine_blk<G>(s, s.hv, s.mu, false);
+    for (int c = tid; c < p; c += G) s.bv[c] = s.hv[c];
+    __syncthreads();
+    for (int k = tid; k < p; k += G)
+      if (s.code[k] < 0 && !s.phan[k]) s.bv[-s.code[k] - 1] = 0.f;
+  }
+  __syncthreads();
+  if (tid == 0) s.flag = ok;
+  __syncthreads();
+}
+
+// (one warp) multipliers from the column sums in red2: right-hand side
+// into mu and hv, mu := B^-T mu (refined by the caller).
+template <int G>
+__device__ __noinline__ void mult_solve(St& s) {
   constexpr int W = G / 32;
   const int lane = lane_id(), p = s.p;
   const float lam = s.lam;
@@ -1094,28 +1269,45 @@ __device__ __noinline__ void multipliers(St& s, bool step) {
     for (int k = 0; k < p; ++k) real |= (s.code[k] == coord_code(c) && !s.phan[k]);
     if (!real) g += lam * fsign(s.bv[c]);
     s.mu[c] = -g;
+    s.hv[c] = -g;  // right-hand side (hv is free after the snap)
   }
   __syncwarp();
   lu_solve_t(s, s.mu);
+}
+
+// (one warp) pick the most violated basis hyperplane (Bland's rule: the
+// lowest id) and, if stepping, the edge direction dv.
+__device__ __noinline__ void mult_pick(St& s, bool step) {
+  const int lane = lane_id(), p = s.p;
+  const float lam = s.lam;
   const float tol = s.a->o.tol_opt * fmaxf(1.f, lam);
-  float worst = tol;
-  int q = -1, phantoms = 0, atcap = 0;
+  float worst = tol, vmax = 0.f;
+  int q = -1, phantoms = 0, atcap = 0, lowest = INT32_MAX, qb = -1;
   for (int k = lane; k < p; k += 32) {
     float cap = s.code[k] >= 0 ? 1.f : (s.phan[k] ? 0.f : lam);
     float viol = fabsf(s.mu[k]) - cap;
     if (s.phan[k]) phantoms++;
     else if (viol > -1e-4f * fmaxf(1.f, cap)) atcap++;
     if (viol > worst) { worst = viol; q = k; }
+    if (viol > tol && s.code[k] < lowest) { lowest = s.code[k]; qb = k; }
+    vmax = fmaxf(vmax, viol);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     float ov = __shfl_xor_sync(0xffffffffu, worst, o);
     int oq = __shfl_xor_sync(0xffffffffu, q, o);
     if (ov > worst || (ov == worst && oq >= 0 && (q < 0 || oq < q))) { worst = ov; q = oq; }
+    int ol = __shfl_xor_sync(0xffffffffu, lowest, o);
+    int oqb = __shfl_xor_sync(0xffffffffu, qb, o);
+    if (ol < lowest) { lowest = ol; qb = oqb; }
   }
+  vmax = warp_max(vmax);
   phantoms = warp_sum_i(phantoms);
   atcap = warp_sum_i(atcap);
-  if (lane == 0) { s.q = q; s.iter = (phantoms > 0 || atcap > 0); }
+  // Bland's rule (release the violating hyperplane of lowest id) while the
+  // polish is not decreasing F: no basis repeats, so no cycling
+  if (s.bland) q = qb;
+  if (lane == 0) { s.q = q; s.iter = (phantoms > 0 || atcap > 0); s.worst = vmax; }
   __syncwarp();
   if (q >= 0 && step) {
     float sg = s.mu[q] > 0.f ? 1.f : -1.f;
@@ -1146,7 +1338,7 @@ __device__ __noinline__ int edge_specials(St& s, int q) {
 // ------------------------------------------------------------------ row passes
 
 // r = y - X b, one column at a time, skipping zero coefficients (b is
-// sparse along most of the path); loads batched kPassU per thread.
+// sparse along most of the path); loads batched kRowU<G> per thread.
 template <int G>
 __device__ __forceinline__ void recompute_r(St& s) {
   const int n = s.n, p = s.p;
@@ -1154,10 +1346,10 @@ __device__ __forceinline__ void recompute_r(St& s) {
   const float* __restrict__ yq = s.yq;
   const float* __restrict__ bv = s.bv;
   float* __restrict__ rr = s.rr;
-  for (int i0 = 0; i0 < n; i0 += G * kPassU) {
-    float v[kPassU];
+  for (int i0 = 0; i0 < n; i0 += G * kRowU<G>) {
+    float v[kRowU<G>];
 #pragma unroll
-    for (int u = 0; u < kPassU; ++u) {
+    for (int u = 0; u < kRowU<G>; ++u) {
       const int i = i0 + u * G + t;
       v[u] = i < n ? yq[i] : 0.f;
     }
@@ -1166,33 +1358,33 @@ __device__ __forceinline__ void recompute_r(St& s) {
       if (b == 0.f) continue;  // uniform
       const float* __restrict__ col = colptr(s, c);
 #pragma unroll
-      for (int u = 0; u < kPassU; ++u) {
+      for (int u = 0; u < kRowU<G>; ++u) {
         const int i = i0 + u * G + t;
         if (i < n) v[u] -= col[i] * b;
       }
     }
 #pragma unroll
-    for (int u = 0; u < kPassU; ++u) {
+    for (int u = 0; u < kRowU<G>; ++u) {
       const int i = i0 + u * G + t;
       if (i < n) rr[i] = v[u];
     }
   }
 }
 
-// r -= d * column (global or shared), loads batched kPassU per thread.
+// r -= d * column (global or shared), loads batched kRowU<G> per thread.
 template <int G>
 __device__ __forceinline__ void axpy_r(St& s, const float* __restrict__ col, float d) {
   const int n = s.n, t = gtid<G>();
   const uint32_t rr_s = smem_u32(s.rr);
-  for (int i0 = 0; i0 < n; i0 += G * kPassU) {
-    float xv[kPassU];
+  for (int i0 = 0; i0 < n; i0 += G * kRowU<G>) {
+    float xv[kRowU<G>];
 #pragma unroll
-    for (int u = 0; u < kPassU; ++u) {
+    for (int u = 0; u < kRowU<G>; ++u) {
       const int i = i0 + u * G + t;
       xv[u] = i < n ? col[i] : 0.f;
     }
 #pragma unroll
-    for (int u = 0; u < kPassU; ++u) {
+    for (int u = 0; u < kRowU<G>; ++u) {
       const int i = i0 + u * G + t;
       if (i < n) sts_f(rr_s + 4u * i, lds_f(rr_s + 4u * i) - xv[u] * d);
     }
@@ -1202,28 +1394,28 @@ __device__ __forceinline__ void axpy_r(St& s, const float* __restrict__ col, flo
 // v_i = x_i . d for the edge direction d into `vd` (shared for one warp,
 // global scratch for a block), zero on basis rows other than the released
 // one (they stay on their hyperplanes along the edge).  Column loads
-// batched kPassU per thread.
+// batched kRowU<G> per thread.
 template <int G>
 __device__ __forceinline__ void edge_products(St& s, float* __restrict__ vd) {
   const int n = s.n, p = s.p, lane = gtid<G>(), qc = s.qcode;
   const float* __restrict__ dv = s.dv;
   const unsigned* __restrict__ mask = s.mask;
-  for (int i0 = 0; i0 < n; i0 += G * kPassU) {
-    float v[kPassU];
+  for (int i0 = 0; i0 < n; i0 += G * kRowU<G>) {
+    float v[kRowU<G>];
 #pragma unroll
-    for (int u = 0; u < kPassU; ++u) v[u] = 0.f;
+    for (int u = 0; u < kRowU<G>; ++u) v[u] = 0.f;
     for (int c = 0; c < p; ++c) {
       const float dc = dv[c];
       if (dc == 0.f) continue;  // uniform; d is zero on basis coordinates
       const float* __restrict__ col = colptr(s, c);
 #pragma unroll
-      for (int u = 0; u < kPassU; ++u) {
+      for (int u = 0; u < kRowU<G>; ++u) {
         const int i = i0 + u * G + lane;
         if (i < n) v[u] += col[i] * dc;
       }
     }
 #pragma unroll
-    for (int u = 0; u < kPassU; ++u) {
+    for (int u = 0; u < kRowU<G>; ++u) {
       const int i = i0 + u * G + lane;
       if (i < n) {
         const bool inb = (mask[i >> 5] >> (i & 31)) & 1u;
@@ -1414,20 +1606,53 @@ __device__ __noinline__ void chop(St& s, int k, int& sweeps, int& probes) {
   gsync<G>();
 }
 
+__device__ __forceinline__ unsigned mix32(unsigned x) {
+  x *= 0x9E3779B1u;
+  x ^= x >> 16;
+  x *= 0x85EBCA6Bu;
+  x ^= x >> 13;
+  x *= 0xC2B2AE35u;
+  x ^= x >> 16;
+  return x;
+}
+
+// (warp 0) order-independent hash of the basis set; s.flag = 1 when it is
+// among the last kHist bases of this polish (then appended).
+__device__ __noinline__ void basis_seen(St& s, int nh) {
+  const int lane = lane_id();
+  unsigned h = 0u;
+  for (int k = lane; k < s.p; k += 32) h += mix32((unsigned)s.code[k] * 2u + (unsigned)s.phan[k]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+  bool seen = false;
+  for (int e = lane; e < min(nh, kHist); e += 32) seen |= s.bhist[e] == h;
+  seen = __any_sync(0xffffffffu, seen);
+  __syncwarp();
+  if (lane == 0) {
+    s.bhist[nh % kHist] = h;
+    s.flag = seen;
+  }
+  __syncwarp();
+}
+
 // Exact polish from the current basis (code/phan); max_piv = 0 only tests.
 template <int G>
 __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonunique) {
   const int tid = gtid<G>(), lane = lane_id(), warp = gwarp<G>();
   const int n = s.n, p = s.p;
-  int it = 0;
+  int it = 0, nh = 0, cycled = 0;  // nh: bases hashed so far
   *is_opt = 0;
   *nonunique = 0;
+  if (tid == 0) s.bland = 0;
   if (G == 32) {
     cp_async_wait_all();  // the column buffers hold edge products below
     __syncwarp();
   }
+  if (warp == 0) basis_seen(s, 0);  // the starting basis
+  gsync<G>();
+  nh = 1;
   for (;;) {
-    if (warp == 0) snap(s);
+    snap_g<G>(s);
     gsync<G>();
     if (!s.flag) break;  // singular basis: give up (status MAX_ITERS)
     recompute_r<G>(s);
@@ -1438,31 +1663,51 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
         if (s.code[k] >= 0) s.mask[s.code[k] >> 5] |= 1u << (s.code[k] & 31);
     gsync<G>();
     // column sums g_c = -sum_{rows not in basis} sign(r_i) x_ic (loads
-    // batched kPassU per thread; per-thread order is row order)
+    // batched kRowU<G> per thread; per-thread order is row order, compensated
+    // summation: at n = 2e4 plain float sums err by ~1e-3 relative)
     for (int c = 0; c < p; ++c) {
       const float* __restrict__ col = colptr(s, c);
-      float a = 0.f;
-      for (int i0 = 0; i0 < n; i0 += G * kPassU) {
-        float xv[kPassU];
+      float a = 0.f, comp = 0.f;
+      for (int i0 = 0; i0 < n; i0 += G * kRowU<G>) {
+        float xv[kRowU<G>];
 #pragma unroll
-        for (int u = 0; u < kPassU; ++u) {
+        for (int u = 0; u < kRowU<G>; ++u) {
           const int i = i0 + u * G + tid;
           xv[u] = i < n ? col[i] : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < kPassU; ++u) {
+        for (int u = 0; u < kRowU<G>; ++u) {
           const int i = i0 + u * G + tid;
-          if (i < n && !((s.mask[i >> 5] >> (i & 31)) & 1u)) a -= fsign(s.rr[i]) * xv[u];
+          if (i < n && !((s.mask[i >> 5] >> (i & 31)) & 1u)) {
+            const float t = -fsign(s.rr[i]) * xv[u] - comp;
+            const float nb = a + t;
+            comp = (nb - a) - t;
+            a = nb;
+          }
         }
       }
-      a = warp_sum(a);
+      a = warp_sum(a) - warp_sum(comp);
       if (lane == 0) s.red2[warp * p + c] = a;
     }
     gsync<G>();
-    if (warp == 0) multipliers<G>(s, it < max_piv);
+    if (warp == 0) mult_solve<G>(s);
+    if (G == 32) refine(s, s.mu, s.hv, true);
+    else refine_blk<G>(s, s.mu, s.hv, true);
+    if (warp == 0) mult_pick(s, it < max_piv);
     gsync<G>();
     const int q = s.q;
     if (q < 0) { *is_opt = 1; *nonunique = s.iter; break; }
+    if (cycled) {
+      // a basis repeated under Bland's rule: each iteration is a function
+      // of the basis alone, so the polish would loop (float32 noise in the
+      // multipliers of a degenerate vertex).  Remaining violations within
+      // float32 resolution accept the vertex as a (non-unique) optimum
+      if (s.worst <= kStallTolFactor * s.a->o.tol_opt * fmaxf(1.f, s.lam)) {
+        *is_opt = 1;
+        *nonunique = 1;
+      }
+      break;
+    }
     if (it >= max_piv) break;
     // edge line search: breakpoints of t -> F(b + t d)
     if (tid == 0) {
@@ -1487,9 +1732,25 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     if (warp == 0) {
       for (int c = lane; c < p; c += 32) s.bv[c] += ts * s.dv[c];
       __syncwarp();
-      if (lane == 0) { s.code[q] = own; s.phan[q] = 0; }
+      if (lane == 0) {
+        s.code[q] = own;
+        s.phan[q] = 0;
+      }
+      __syncwarp();
+      basis_seen(s, nh);
     }
     gsync<G>();
+    // group-uniform: every thread reads the same flag.  A repeated basis
+    // switches the release rule to Bland's (lowest id), which does not
+    // cycle in exact arithmetic; a repeat under Bland's rule ends the polish
+    const int rep_seen = s.flag;
+    ++nh;
+    if (rep_seen) {
+      if (s.bland) cycled = 1;
+      nh = 0;  // fresh history for the new rule
+    }
+    gsync<G>();
+    if (tid == 0 && rep_seen) s.bland = 1;
     ++it;
   }
   gsync<G>();
@@ -1499,7 +1760,7 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
 // F at the vertex of the current basis (snap; +inf when singular).
 template <int G>
 __device__ __noinline__ float vertex_objective(St& s) {
-  if (gwarp<G>() == 0) snap(s);
+  snap_g<G>(s);
   gsync<G>();
   if (!s.flag) return kInf;
   recompute_r<G>(s);
@@ -1717,7 +1978,7 @@ __host__ __device__ size_t group_smem_bytes(int ncap, int P) {
   size_t colbuf = G == 32 ? 2 * (size_t)ncap : 0;
   size_t words = (size_t)ncap + colbuf + sel_bm + 7 * (size_t)P + (size_t)W * P +
                  9 * (size_t)P + 3 * ((size_t)P + 1) + (size_t)ncap / 32 + 1 +
-                 2 * (size_t)W * 16 + 64 + W;
+                 2 * (size_t)W * 16 + 64 + W + kHist;
   return ((words * 4 + 15) / 16) * 16;
 }
 
@@ -1744,6 +2005,7 @@ __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   }
   s.bv = f; f += P; s.bbest = f; f += P; s.dv = f; f += P;
   s.mu = f; f += P; s.tv = f; f += P; s.hv = f; f += P; s.dl = f; f += P;
+  s.rv = s.dv;  // refinement scratch: dv is free whenever a solve is refined
   s.red2 = f; f += W * P;
   int* ip = reinterpret_cast<int*>(f);
   s.code = ip; ip += P; s.phan = ip; ip += P; s.piv = ip; ip += P; s.perm = ip; ip += P;
@@ -1759,6 +2021,7 @@ __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   s.sampk = f; f += 32;
   s.sampw = f; f += 32;
   s.wcnt = reinterpret_cast<int*>(f); f += W;
+  s.bhist = reinterpret_cast<unsigned*>(f); f += kHist;
 }
 
 template <int G, int NW>

@@ -12,6 +12,18 @@ namespace ll {
 namespace {
 
 constexpr float kInf = INFINITY;
+constexpr int kHist = 32;               // polish: bases remembered for cycle detection
+constexpr float kStallTolFactor = 50.f; // cycling vertex accepted when violations are below this x tol
+
+__device__ __forceinline__ unsigned mix32(unsigned x) {
+  x *= 0x9E3779B1u;
+  x ^= x >> 16;
+  x *= 0x85EBCA6Bu;
+  x ^= x >> 13;
+  x *= 0xC2B2AE35u;
+  x ^= x >> 16;
+  return x;
+}
 
 struct TFit {
   // problem
@@ -308,6 +320,29 @@ struct TFit {
     for (int c = 0; c < p; ++c) xv[perm[c]] = tv[c];
   }
 
+  // One step of iterative refinement of x solving B x = h (trans false) or
+  // B^T x = h (trans true): residual in FP64 from the basis normals (exact
+  // in FP32), correction from the FP32 factors; `rs` is scratch [p].
+  __device__ void refine(float* xv, const float* h, float* rs, bool trans) {
+    for (int e = 0; e < p; ++e) {
+      double acc = 0.0;
+      if (!trans) {
+        const int cd = code[e];
+        if (cd >= 0) for (int c = 0; c < p; ++c) acc += (double)x(cd, c) * (double)xv[c];
+        else acc = (double)xv[-cd - 1];
+      } else {
+        for (int k = 0; k < p; ++k) {
+          const int cd = code[k];
+          const float nv = cd >= 0 ? x(cd, e) : (e == -cd - 1 ? 1.f : 0.f);
+          acc += (double)nv * (double)xv[k];
+        }
+      }
+      rs[e] = (float)((double)h[e] - acc);
+    }
+    if (trans) lu_solve_t(rs); else lu_solve(rs);
+    for (int e = 0; e < p; ++e) xv[e] += rs[e];
+  }
+
   __device__ bool in_basis_row(int i) const {
     for (int k = 0; k < p; ++k) if (code[k] == i) return true;
     return false;
@@ -321,8 +356,10 @@ struct TFit {
       int cd = code[k];
       hv[k] = cd >= 0 ? yv(cd) : (phan[k] ? bv[-cd - 1] : 0.f);
     }
+    for (int k = 0; k < p; ++k) mu[k] = hv[k];  // right-hand side (mu is free here)
     if (!lu()) return false;
     lu_solve(hv);
+    refine(hv, mu, dv, false);
     for (int c = 0; c < p; ++c) bv[c] = hv[c];
     for (int k = 0; k < p; ++k) if (code[k] < 0 && !phan[k]) bv[-code[k] - 1] = 0.f;
     recompute_r();
@@ -346,35 +383,62 @@ struct TFit {
     recompute_r();
   }
 
+  // order-independent hash of the basis set
+  __device__ unsigned basis_hash() const {
+    unsigned h = 0u;
+    for (int k = 0; k < p; ++k) h += mix32((unsigned)code[k] * 2u + (unsigned)phan[k]);
+    return h;
+  }
+
   __device__ int polish(int max_piv, int& is_opt, int& nonunique) {
     const float tol = a->o.tol_opt * fmaxf(1.f, lam);
-    int it = 0;
+    // recent bases: a repeat switches to Bland's rule, a repeat under it
+    // ends the polish (each iteration is a function of the basis alone)
+    unsigned hist[kHist];
+    int it = 0, nh = 1, bland = 0, cycled = 0;
+    hist[0] = basis_hash();
     is_opt = 0;
     nonunique = 0;
     for (;;) {
       if (!snap()) break;
-      for (int c = 0; c < p; ++c) mu[c] = 0.f;
+      // mu = -g, row part with compensated sums
+      for (int c = 0; c < p; ++c) { mu[c] = 0.f; tv[c] = 0.f; }
       for (int i = 0; i < n; ++i) {
         if (in_basis_row(i)) continue;
-        float s = fsign(r[i]);
-        if (s != 0.f) for (int c = 0; c < p; ++c) mu[c] += s * x(i, c);  // mu = -g (row part)
+        float sg = fsign(r[i]);
+        if (sg != 0.f)
+          for (int c = 0; c < p; ++c) {
+            const float t = sg * x(i, c) - tv[c];
+            const float nb = mu[c] + t;
+            tv[c] = (nb - mu[c]) - t;
+            mu[c] = nb;
+          }
       }
       for (int c = 0; c < p; ++c) {
         bool real = false;
         for (int k = 0; k < p; ++k) real |= (code[k] == coord_code(c) && !phan[k]);
         if (!real) mu[c] -= lam * fsign(bv[c]);
+        hv[c] = mu[c];  // right-hand side (hv is free after the snap)
       }
       lu_solve_t(mu);
-      int qq = -1, phantoms = 0, atcap = 0;
-      float worst = tol;
+      refine(mu, hv, dv, true);
+      int qq = -1, qb = -1, lowest = INT32_MAX, phantoms = 0, atcap = 0;
+      float worst = tol, vmax = 0.f;
       for (int k = 0; k < p; ++k) {
         float cap = code[k] >= 0 ? 1.f : (phan[k] ? 0.f : lam);
         float viol = fabsf(mu[k]) - cap;
         if (phan[k]) phantoms++;
         else if (viol > -1e-4f * fmaxf(1.f, cap)) atcap++;
         if (viol > worst) { worst = viol; qq = k; }
+        if (viol > tol && code[k] < lowest) { lowest = code[k]; qb = k; }
+        vmax = fmaxf(vmax, viol);
       }
+      if (bland) qq = qb;  // Bland's rule: lowest id
       if (qq < 0) { is_opt = 1; nonunique = phantoms > 0 || atcap > 0; break; }
+      if (cycled) {
+        if (vmax <= kStallTolFactor * tol) { is_opt = 1; nonunique = 1; }
+        break;
+      }
       if (it >= max_piv) break;
       float sg = mu[qq] > 0.f ? 1.f : -1.f;
       for (int c = 0; c < p; ++c) dv[c] = c == qq ? sg : 0.f;
@@ -403,6 +467,16 @@ struct TFit {
       for (int c = 0; c < p; ++c) bv[c] += ts * dv[c];
       code[qq] = own;
       phan[qq] = 0;
+      const unsigned h = basis_hash();
+      bool seen = false;
+      for (int e = 0; e < min(nh, kHist); ++e) seen |= hist[e] == h;
+      hist[nh % kHist] = h;
+      ++nh;
+      if (seen) {
+        if (bland) cycled = 1;
+        bland = 1;
+        nh = 0;
+      }
       ++it;
     }
     return it;

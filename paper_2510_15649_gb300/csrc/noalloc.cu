@@ -17,6 +17,7 @@ int launch_group(const ladlasso_dims* d);
 cudaError_t launch_validate_offsets(const int64_t* offsets, int B, int64_t total_rows, int* ctrl,
                                     cudaStream_t st);
 cudaError_t launch_order(const int64_t* offsets, const int32_t* nr, const int32_t* p, int P, int B,
+                         int policy,
                          int* order, cudaStream_t st);
 int fit_block_group(int n_max);
 int fit_block_max_rows(int G, int P);
@@ -66,7 +67,8 @@ extern "C" int ladlasso_fit_batched_noalloc(const float* X, const float* y, cons
                                                 (size_t)xg_slots((int)P4) * sizeof(float);
   if (need > kScratchBytes) return LADLASSO_ERR_NOMEM;  // problem set too large for the fixed array
   const int G = launch_group(d);
-  if (G == 0 || d->fits_per_block < 0) return LADLASSO_ERR_INVALID;
+  if (G == 0 || d->fits_per_block < 0 || d->work_order < 0 || d->work_order > 1)
+    return LADLASSO_ERR_INVALID;
   if (d->n_max > fit_block_max_rows(G, d->P_cols)) return LADLASSO_ERR_NOMEM;
   if (d->B == 0) return LADLASSO_OK;
   unsigned char* base = nullptr;
@@ -106,7 +108,8 @@ extern "C" int ladlasso_fit_batched_noalloc(const float* X, const float* y, cons
   if (cudaMemsetAsync(a.queue, 0, 256, st) != cudaSuccess) return LADLASSO_ERR_CUDA;
   if (launch_validate_offsets(offsets, a.B, a.total_rows, a.queue, st) != cudaSuccess)
     return LADLASSO_ERR_CUDA;
-  if (launch_order(offsets, a.n_rows, a.p, a.P, a.B, a.order, st) != cudaSuccess) return LADLASSO_ERR_CUDA;
+  if (launch_order(offsets, a.n_rows, a.p, a.P, a.B, d->work_order, a.order, st) != cudaSuccess)
+    return LADLASSO_ERR_CUDA;
   return launch_fit_block(a, st, sms, G, d->fits_per_block) == cudaSuccess ? LADLASSO_OK
                                                                           : LADLASSO_ERR_CUDA;
 }

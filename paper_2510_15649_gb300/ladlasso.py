@@ -40,7 +40,8 @@ class Dims(C.Structure):
                 ("p", C.c_void_p), ("n_rows", C.c_void_p), ("b_init", C.c_void_p), ("fit_status", C.c_void_p),
                 ("basis_out", C.c_void_p), ("counters", C.c_void_p), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t), ("opts", C.c_void_p),
-                ("group_threads", C.c_int32), ("fits_per_block", C.c_int32)]
+                ("group_threads", C.c_int32), ("fits_per_block", C.c_int32),
+                ("work_order", C.c_int32)]
 
 
 class LadLassoError(RuntimeError):
@@ -196,6 +197,7 @@ class Launch:
     .fits_per_block; zeros = the library's automatic choice)."""
     group_threads: int = 0
     fits_per_block: int = 0
+    work_order: int = 0
 
 
 def launch_shape(pr: Problems, launch: Launch | None = None) -> tuple:
@@ -235,6 +237,7 @@ def fit(pr: Problems, lambdas: torch.Tensor, *, b_init=None, opts: Opts | None =
                 counters=out.get("counters"))
     if launch is not None:
         d.group_threads, d.fits_per_block = launch.group_threads, launch.fits_per_block
+        d.work_order = launch.work_order
     fn = lib().ladlasso_fit_batched_thread if per_thread else lib().ladlasso_fit_batched
     _check(fn(_ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), _ptr(lam.contiguous()),
               _ptr(out["b"]), _ptr(out["obj"]), C.byref(d), _stream(stream)))

@@ -2,9 +2,10 @@
 
 The fit kernel has two shapes (one warp per fit with several fits per
 thread block, or one 512-thread block per fit) and, for the one-warp shape,
-a number of fits per block bounded by shared memory.  More fits per block
+a number of fits per block bounded by shared memory; problems are taken
+longest first or longest and shortest alternately.  More fits per block
 hide more latency but also keep more gathered designs live in L2 at once,
-so the best count depends on the problem mix.  `autotune` times every
+so the best choice depends on the problem mix.  `autotune` times every
 candidate on an evenly strided sample of the problem set (same size mix)
 with CUDA events and returns the fastest; choices are cached per device and
 problem-set signature.  Per-fit results do not depend on fits_per_block;
@@ -24,12 +25,13 @@ def candidates(pr: ll.Problems) -> list:
     """Launch shapes the library accepts for `pr`."""
     out = []
     g, fmax, mrows = ll.launch_shape(pr, ll.Launch(32, 0))
-    if pr.n_max <= mrows:
-        lo = max(1, fmax // 2)
-        out += [ll.Launch(32, f) for f in range(fmax, lo - 1, -1)]
+    for order in (0, 1):
+        if pr.n_max <= mrows:
+            lo = max(1, fmax // 3)
+            out += [ll.Launch(32, f, order) for f in range(fmax, lo - 1, -1)]
     g, _, mrows = ll.launch_shape(pr, ll.Launch(512, 0))
     if pr.n_max <= mrows:
-        out.append(ll.Launch(512, 0))
+        out += [ll.Launch(512, 0, 0), ll.Launch(512, 0, 1)]
     return out
 
 
