@@ -39,16 +39,23 @@ namespace {
 constexpr float kInf = INFINITY;
 constexpr int kSampM = 3;      // bracket half-width (samples) on buffer levels
 constexpr int kWinM = 4;       // bracket half-width (samples) for pass windows
-constexpr int kU = 4;          // elements per thread per compaction chunk
+#ifndef LL_KU
+#define LL_KU 1
+#endif
+#ifndef LL_PASSU
+#define LL_PASSU 2
+#endif
+#ifndef LL_ROWU
+#define LL_ROWU 4
+#endif
+constexpr int kU = LL_KU;      // elements per thread per compaction chunk
 constexpr int kBufCap = 256;   // selection buffer of the one-warp path
 constexpr int kMaxPasses = 64; // cap on fused passes per 1-D step
-constexpr int kAxis = 0, kEdge = 1;
 constexpr int kSubCap = 128;   // block path: selection sub-buffer per warp
 constexpr int kBlockG = 512;   // block path: threads per fit
 constexpr int kHist = 32;               // polish: bases remembered for cycle detection
+constexpr int kChgW = 64;               // block polish: changed rows per warp before a full recompute
 constexpr float kStallTolFactor = 50.f; // cycling vertex accepted when violations are below this x tol
-// dynamic shared memory one block may take: 227 KB less the static state
-constexpr size_t kDynSmemLimit = 227 * 1024 - 8 * 1024;
 
 // Uniform per-group state, resident in shared memory.
 struct St {
@@ -62,6 +69,10 @@ struct St {
   int* code_prev; int* phan_prev;  // [P] last path position's final basis
   int* code_alt; int* phan_alt;    // [P] the other polish start
   unsigned* bhist;                 // [kHist] hashes of the polish's recent bases
+  // block path, incremental column sums of the polish:
+  signed char* sgn;                // [ncap] sign of row i in the last sums (0 in basis)
+  double* gd;                      // [P] g_c = -sum_i sgn_i x_ic
+  int* chg;                        // [W * kChgW] changed rows, packed (i << 2) | (delta + 2)
   float* sk; float* sw; int* sid;      // special breakpoints [P+1]
   unsigned* mask;                      // basis-row bitmap [maskw]
   float* redf; int* redi;              // reductions [W*16]
@@ -74,8 +85,10 @@ struct St {
   float* cb[2];      // one warp: double-buffered copy of the current column
   int cur;           // buffer holding the column of the current axis step
   const float* yq;   // targets
-  const float* colp; // current column (axis steps)
-  const float* vd;   // one warp, polish: v_i = x_i . d of the edge (a column buffer)
+  const float* colp; // per-row factor of the current 1-D problem: the column
+                     // (axis step) or the edge products x_i . d (polish)
+  float pbase;       // key offset: b_j (axis step) or 0 (edge line search)
+  int pq;            // row whose key is pinned at 0 (the released basis row), or -1
   int n, p, ld, nspec, qcode;
   float lam, bj;
   // broadcast slots
@@ -88,6 +101,11 @@ struct St {
   // per-fit counters
   int passes, selects, sel_fail;
 };
+
+// dynamic shared memory one block may take: 227 KB less the static state of
+// the one-warp kernel (16 group states and the argument copy)
+constexpr size_t kDynSmemLimit =
+    227 * 1024 - ((16 * sizeof(St) + sizeof(FitArgs) + 256 + 1023) / 1024) * 1024;
 
 template <int G> __device__ __forceinline__ int gtid() { return G == 32 ? (threadIdx.x & 31) : threadIdx.x; }
 template <int G> __device__ __forceinline__ int gwarp() { return G == 32 ? 0 : (threadIdx.x >> 5); }
@@ -431,31 +449,16 @@ __device__ __forceinline__ const float* colptr(const St& s, int c) {
 
 // ------------------------------------------------------------------ one-warp fused selection
 
-// Breakpoint of row i for the current 1-D problem.
-//   kAxis: z = b_j + r_i / x_ij, weight |x_ij|            (axis step)
-//   kEdge: t = r_i / v_i with v_i = x_i . d, weight |v_i|  (polish edge);
-//          basis rows other than the released one stay on their hyperplanes
-template <int MODE>
+// Breakpoint of row i for the current 1-D problem, one formula for both:
+//   axis step:  x_i = x_ij,     key b_j + r_i / x_i  (pbase = b_j, pq = -1)
+//   polish edge: x_i = x_i . d,  key r_i / x_i        (pbase = 0), the released
+//               basis row pinned at 0; other basis rows have x_i = 0
+// weight |x_i|; x_i = 0 gives key +inf and no weight.
 __device__ __forceinline__ void row_key(const St& s, int i, float& k, float& w) {
-  if (MODE == kAxis) {
-    const float x = s.colp[i];
-    k = x != 0.f ? s.bj + __fdividef(s.rr[i], x) : kInf;
-    w = fabsf(x);
-  } else {
-    float v = 0.f;
-    if (s.vd) {
-      v = s.vd[i];  // basis rows other than the released one already hold 0
-    } else {
-      for (int c = 0; c < s.p; ++c) {
-        const float dc = s.dv[c];
-        if (dc != 0.f) v += xval(s, c, i) * dc;  // d is zero on basis coordinates
-      }
-      const bool inb = (s.mask[i >> 5] >> (i & 31)) & 1u;
-      if (inb && i != s.qcode) v = 0.f;
-    }
-    k = i == s.qcode ? 0.f : (v != 0.f ? __fdividef(s.rr[i], v) : kInf);
-    w = fabsf(v);
-  }
+  const float x = s.colp[i];
+  k = x != 0.f ? s.pbase + __fdividef(s.rr[i], x) : kInf;
+  if (i == s.pq) k = 0.f;
+  w = fabsf(x);
 }
 
 // (one warp) one pass over rows and specials against the window [lo, hi]:
@@ -464,13 +467,14 @@ __device__ __forceinline__ void row_key(const St& s, int i, float& k, float& w) 
 // selects it), total, count inside, smallest key above hi; the first
 // kBufCap keys inside go to the buffer (row order, then specials).  Rows
 // are taken kPassU per lane at a time so their loads overlap.
-constexpr int kPassU = 8;
+constexpr int kPassU = LL_PASSU;
 // rows per thread per batch in the whole-design loops (residual, edge
 // products, column sums), which read the gathered design straight from L2
-// or HBM: 16 loads in flight per thread.  The rows a thread visits, and
-// their order, do not depend on it.
+// or HBM.  The block path keeps 16 loads in flight per thread; the one-warp
+// path keeps its unrolled code small (instruction-cache pressure).  The
+// rows a thread visits, and their order, do not depend on it.
 template <int G>
-constexpr int kRowU = 16;
+constexpr int kRowU = G == 32 ? LL_ROWU : 16;
 
 // The buffer pointers are passed in registers (restrict-qualified): going
 // through the shared state struct would reload them after every store.
@@ -491,11 +495,10 @@ __device__ __forceinline__ void classify_one(float* __restrict__ bk, float* __re
 }
 
 // Rows from shared memory (a per-row factor x_i and the residual r_i):
-//   kAxis: x_i = x_ij,     z = b_j + r_i / x_i, weight |x_i|
-//   kEdge: x_i = x_i . d,  t = r_i / x_i (0 for the released row `qc`)
+//   axis step:   x_i = x_ij,     z = b_j + r_i / x_i, weight |x_i|  (bj = b_j, qc = -1)
+//   polish edge: x_i = x_i . d,  t = r_i / x_i (0 for the released row qc)  (bj = 0)
 // Batches of 32 * kPassU rows; the compaction code runs only when some lane
 // of the warp holds a key inside the window.
-template <int MODE>
 __device__ __forceinline__ void smem_rows(uint32_t col_s, uint32_t rr_s, float bj, int qc, int n,
                                           float lo, float hi, uint32_t bk_s, uint32_t bw_s,
                                           uint32_t bi_s, float& al, float& ale, float& at,
@@ -516,9 +519,8 @@ __device__ __forceinline__ void smem_rows(uint32_t col_s, uint32_t rr_s, float b
       const int e = i0 + u * 32 + lane;
       const float x = xv[u];  // zero beyond n: no weight, key +inf
       const float w = fabsf(x);
-      float k;
-      if (MODE == kAxis) k = x != 0.f ? bj + __fdividef(rv[u], x) : kInf;
-      else k = e == qc ? 0.f : (x != 0.f ? __fdividef(rv[u], x) : kInf);
+      float k = x != 0.f ? bj + __fdividef(rv[u], x) : kInf;
+      if (e == qc) k = 0.f;
       at += w;
       al += k < lo ? w : 0.f;
       ale += k <= hi ? w : 0.f;
@@ -538,7 +540,6 @@ __device__ __forceinline__ void smem_rows(uint32_t col_s, uint32_t rr_s, float b
   }
 }
 
-template <int MODE>
 __device__ __noinline__ void fused_pass(St& s, float lo, float hi) {
   const int lane = lane_id();
   const int n = s.n, nspec = s.nspec;
@@ -547,20 +548,9 @@ __device__ __noinline__ void fused_pass(St& s, float lo, float hi) {
   int* __restrict__ bi = s.cid;
   float al = 0.f, ale = 0.f, at = 0.f, amin = kInf;
   int base = 0;
-  if (MODE == kAxis) {
-    smem_rows<kAxis>(smem_u32(s.colp), smem_u32(s.rr), s.bj, 0, n, lo, hi, smem_u32(bk),
-                     smem_u32(bw), smem_u32(bi), al, ale, at, amin, base);
-  } else if (s.vd) {
-    smem_rows<kEdge>(smem_u32(s.vd), smem_u32(s.rr), 0.f, s.qcode, n, lo, hi, smem_u32(bk),
-                     smem_u32(bw), smem_u32(bi), al, ale, at, amin, base);
-  } else {
-    for (int i0 = 0; i0 < n; i0 += 32) {
-      const int e = i0 + lane;
-      float k = kInf, w = 0.f;
-      if (e < n) row_key<MODE>(s, e, k, w);
-      classify_one(bk, bw, bi, k, w, e, e < n, lo, hi, al, ale, at, amin, base, kBufCap);
-    }
-  }
+  // one warp: the per-row factors are in shared memory (a column buffer)
+  smem_rows(smem_u32(s.colp), smem_u32(s.rr), s.pbase, s.pq, n, lo, hi, smem_u32(bk),
+            smem_u32(bw), smem_u32(bi), al, ale, at, amin, base);
   const float* __restrict__ sk = s.sk;
   const float* __restrict__ sw = s.sw;
   const int* __restrict__ sid = s.sid;
@@ -584,8 +574,8 @@ __device__ __noinline__ void fused_pass(St& s, float lo, float hi) {
 // buffer entries when `nbuf` > 0.  Fewer than 8 samples inside: the whole
 // interval.
 // (one warp) the window from one sampled key per lane (k, w).
-__device__ __forceinline__ void window_from_samples(St& s, float k, float w, float rl, float ru,
-                                                    float frac) {
+__device__ __noinline__ void window_from_samples(St& s, float k, float w, float rl, float ru,
+                                                 float frac) {
   const int lane = lane_id();
   const bool ok = k > rl && k < ru && w > 0.f;
   if (!ok) { k = kInf; w = 0.f; }
@@ -609,7 +599,6 @@ __device__ __forceinline__ void window_from_samples(St& s, float k, float w, flo
   __syncwarp();
 }
 
-template <int MODE>
 __device__ __noinline__ void region_window(St& s, float rl, float ru, float frac, int nbuf) {
   const int lane = lane_id();
   const int n = s.n;
@@ -620,7 +609,7 @@ __device__ __noinline__ void region_window(St& s, float rl, float ru, float frac
     w = s.cw[e];
   } else if (n > 0) {
     const int i = n >= 32 ? (int)(((int64_t)lane * n) / 32) : lane;
-    if (i < n) row_key<MODE>(s, i, k, w);
+    if (i < n) row_key(s, i, k, w);
   }
   window_from_samples(s, k, w, rl, ru, frac);
 }
@@ -628,20 +617,19 @@ __device__ __noinline__ void region_window(St& s, float rl, float ru, float frac
 // (one warp) weighted median of the current 1-D problem (rows via row_key,
 // specials in sk/sw/sid).  With `prior`, the first window is [lo0, hi0].
 // Result in s.zstar / s.owner.
-template <int MODE>
 __device__ __noinline__ void select_fused(St& s, float cur, bool prior, float lo0, float hi0) {
   const int lane = lane_id();
   float rl = -kInf, ru = kInf;  // open interval known to hold the target
   float wrl = 0.f, wru = -1.f;  // weight of keys <= rl, < ru
   float lo = lo0, hi = hi0;
   if (!prior) {
-    region_window<MODE>(s, rl, ru, 0.5f, 0);
+    region_window(s, rl, ru, 0.5f, 0);
     lo = s.lo; hi = s.hi;
   }
   float half = -1.f;
   if (lane == 0) s.selects++;
   for (int it = 0; it < kMaxPasses; ++it) {
-    fused_pass<MODE>(s, lo, hi);
+    fused_pass(s, lo, hi);
     if (lane == 0) s.passes++;
     const float wl = s.p_wl, wle = s.p_wi, wt = s.p_wt;
     const int cnt = s.p_cnt;
@@ -657,16 +645,16 @@ __device__ __noinline__ void select_fused(St& s, float cur, bool prior, float lo
     }
     if (half <= wl) {                       // target below the window
       ru = lo; wru = wl;
-      region_window<MODE>(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
+      region_window(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
     } else if (half > wle) {                // target above the window
       rl = hi; wrl = wle;
-      region_window<MODE>(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
+      region_window(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
     } else if (cnt <= kBufCap) {            // target inside, all keys buffered
       select_buf<32>(s, cnt, cur, 0, wl, half, s.p_amin, wle - wl);
       return;
     } else {                                // inside but too many keys: narrow
       rl = next_down(lo); ru = next_up(hi); wrl = wl; wru = wle;
-      region_window<MODE>(s, rl, ru, (half - wl) / fmaxf(wle - wl, 1e-30f), kBufCap);
+      region_window(s, rl, ru, (half - wl) / fmaxf(wle - wl, 1e-30f), kBufCap);
       if (s.lo == lo && s.hi == hi) {
         // no narrower window from the samples (keys tie at the ends): finish
         // on the buffered keys, which begin the window in row order
@@ -691,14 +679,14 @@ __device__ __noinline__ void select_fused(St& s, float cur, bool prior, float lo
 // The per-row factor (the column for axis steps, the edge products for the
 // polish) is read from global memory, the residual from shared memory.
 
-template <int G, int MODE>
+template <int G>
 __device__ __noinline__ void fused_pass_blk(St& s, float lo, float hi) {
   constexpr int W = G / 32;
   const int lane = lane_id(), warp = gwarp<G>(), tid = gtid<G>();
   const int n = s.n, nspec = s.nspec;
-  const float* __restrict__ xs = MODE == kAxis ? s.colp : s.vd;
-  const float bj = s.bj;
-  const int qc = s.qcode;
+  const float* __restrict__ xs = s.colp;
+  const float bj = s.pbase;
+  const int qc = s.pq;
   const uint32_t rr_s = smem_u32(s.rr);
   float* __restrict__ bk = s.ck + warp * kSubCap;
   float* __restrict__ bw = s.cw + warp * kSubCap;
@@ -721,9 +709,8 @@ __device__ __noinline__ void fused_pass_blk(St& s, float lo, float hi) {
       const int e = i0 + u * 32 + lane;
       const float x = xv[u];  // zero beyond n: no weight, key +inf
       const float w = fabsf(x);
-      float k;
-      if (MODE == kAxis) k = x != 0.f ? bj + __fdividef(rv[u], x) : kInf;
-      else k = e == qc ? 0.f : (x != 0.f ? __fdividef(rv[u], x) : kInf);
+      float k = x != 0.f ? bj + __fdividef(rv[u], x) : kInf;
+      if (e == qc) k = 0.f;
       at += w;
       al += k < lo ? w : 0.f;
       ale += k <= hi ? w : 0.f;
@@ -828,7 +815,7 @@ __device__ __noinline__ void sub_window(St& s, float rl, float ru, float frac) {
 }
 
 // Block version of select_fused (same contract).
-template <int G, int MODE>
+template <int G>
 __device__ __noinline__ void select_fused_blk(St& s, float cur, bool prior, float lo0, float hi0) {
   const int tid = gtid<G>(), warp = gwarp<G>();
   float rl = -kInf, ru = kInf;  // open interval known to hold the target
@@ -836,14 +823,14 @@ __device__ __noinline__ void select_fused_blk(St& s, float cur, bool prior, floa
   float lo = lo0, hi = hi0;
   gsync<G>();
   if (!prior) {
-    if (warp == 0) region_window<MODE>(s, rl, ru, 0.5f, 0);
+    if (warp == 0) region_window(s, rl, ru, 0.5f, 0);
     gsync<G>();
     lo = s.lo; hi = s.hi;
   }
   float half = -1.f;
   if (tid == 0) s.selects++;
   for (int it = 0; it < kMaxPasses; ++it) {
-    fused_pass_blk<G, MODE>(s, lo, hi);
+    fused_pass_blk<G>(s, lo, hi);
     if (tid == 0) s.passes++;
     const float wl = s.p_wl, wle = s.p_wi, wt = s.p_wt, amin = s.p_amin;
     const int cnt = s.p_cnt, ovf = s.p_ovf;
@@ -859,10 +846,10 @@ __device__ __noinline__ void select_fused_blk(St& s, float cur, bool prior, floa
     }
     if (half <= wl) {                       // target below the window
       ru = lo; wru = wl;
-      if (warp == 0) region_window<MODE>(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
+      if (warp == 0) region_window(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
     } else if (half > wle) {                // target above the window
       rl = hi; wrl = wle;
-      if (warp == 0) region_window<MODE>(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
+      if (warp == 0) region_window(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
     } else if (!ovf) {                      // target inside, all keys buffered
       compact_sub<G>(s);
       select_buf<G>(s, cnt, cur, 0, wl, half, amin, wle - wl);
@@ -1320,10 +1307,14 @@ __device__ __noinline__ void mult_pick(St& s, bool step) {
 // (thread 0) coordinate breakpoints of the edge line search into sk/sw/sid.
 __device__ __noinline__ int edge_specials(St& s, int q) {
   const int p = s.p;
+  // coordinate -> basis position (perm is free until the next factorisation)
+  int* pos = s.perm;
+  for (int c = 0; c < p; ++c) pos[c] = -1;
+  for (int k = 0; k < p; ++k)
+    if (s.code[k] < 0) pos[-s.code[k] - 1] = k;
   int ns = 0;
   for (int c = 0; c < p; ++c) {
-    int kk = -1;
-    for (int k = 0; k < p; ++k) if (s.code[k] == coord_code(c)) kk = k;
+    const int kk = pos[c];
     if (kk >= 0 && kk != q) continue;  // other basis coordinates stay at 0
     float dc = s.dv[c];
     if (kk == q && !s.phan[q]) {
@@ -1340,7 +1331,7 @@ __device__ __noinline__ int edge_specials(St& s, int q) {
 // r = y - X b, one column at a time, skipping zero coefficients (b is
 // sparse along most of the path); loads batched kRowU<G> per thread.
 template <int G>
-__device__ __forceinline__ void recompute_r(St& s) {
+__device__ __noinline__ void recompute_r(St& s) {
   const int n = s.n, p = s.p;
   const int t = gtid<G>();
   const float* __restrict__ yq = s.yq;
@@ -1373,7 +1364,7 @@ __device__ __forceinline__ void recompute_r(St& s) {
 
 // r -= d * column (global or shared), loads batched kRowU<G> per thread.
 template <int G>
-__device__ __forceinline__ void axpy_r(St& s, const float* __restrict__ col, float d) {
+__device__ __noinline__ void axpy_r(St& s, const float* __restrict__ col, float d) {
   const int n = s.n, t = gtid<G>();
   const uint32_t rr_s = smem_u32(s.rr);
   for (int i0 = 0; i0 < n; i0 += G * kRowU<G>) {
@@ -1436,7 +1427,7 @@ __device__ __forceinline__ void prefetch_col(St& s, int j, int buf) {
 }
 
 template <int G>
-__device__ __forceinline__ float objective(St& s) {
+__device__ __noinline__ float objective(St& s) {
   float a = 0.f;
   for (int i = gtid<G>(); i < s.n; i += G) a += fabsf(s.rr[i]);
   float b = 0.f;
@@ -1470,14 +1461,16 @@ __device__ __noinline__ float axis_update(St& s, int j, int jnext) {
   if (gtid<G>() == 0) {
     s.colp = col;
     s.bj = bj;
+    s.pbase = bj;
+    s.pq = -1;
     s.nspec = s.lam > 0.f ? 1 : 0;
     s.sk[0] = 0.f; s.sw[0] = s.lam; s.sid[0] = coord_code(j);
   }
   gsync<G>();
   {
     const float dl = s.dl[j];
-    if (G == 32) select_fused<kAxis>(s, bj, true, bj - dl, bj + dl);
-    else select_fused_blk<G, kAxis>(s, bj, true, bj - dl, bj + dl);
+    if (G == 32) select_fused(s, bj, true, bj - dl, bj + dl);
+    else select_fused_blk<G>(s, bj, true, bj - dl, bj + dl);
   }
   const float z = s.zstar;
   const int own = s.owner;
@@ -1527,7 +1520,7 @@ __device__ __noinline__ int ccd(St& s, int skip, int max_sweeps) {
 
 // One chop probe: b_k := t, restricted CCD from the previous probe's point.
 template <int G>
-__device__ __forceinline__ float probe(St& s, int k, float t, float& best_f, int& sweeps,
+__device__ __noinline__ float probe(St& s, int k, float t, float& best_f, int& sweeps,
                                        int& probes) {
   const float d = t - s.bv[k];
   if (d != 0.f) axpy_r<G>(s, colptr(s, k), d);
@@ -1606,6 +1599,114 @@ __device__ __noinline__ void chop(St& s, int k, int& sweeps, int& probes) {
   gsync<G>();
 }
 
+// (all G threads, block path) the polish's column sums
+//   g_c = -sum_{rows not in basis} sign(r_i) x_ic
+// into red2 (warp 0's slot; the others 0).  `full`: every column over every
+// row (compensated float sums per thread, FP64 across warps), remembering
+// each row's sign.  Otherwise only rows whose sign or basis membership
+// changed since the last sums contribute, g kept in FP64: at p = 128,
+// n = 2e4 the full sums are 2.6 M loads per pivot, the changes typically a
+// few hundred.  More than kChgW changed rows in some warp falls back to full.
+template <int G>
+__device__ __noinline__ void colsums_blk(St& s, bool full) {
+  constexpr int W = G / 32;
+  const int tid = gtid<G>(), lane = lane_id(), warp = gwarp<G>();
+  const int n = s.n, p = s.p;
+  if (!full) {
+    // changed rows, per warp in row order (warp w: row chunks w, w + W, ...)
+    int cnt = 0;
+    for (int i0 = warp * 32; i0 < n; i0 += G) {
+      const int i = i0 + lane;
+      int d = 0;
+      if (i < n) {
+        const bool inb = (s.mask[i >> 5] >> (i & 31)) & 1u;
+        const int st = inb ? 0 : (int)fsign(s.rr[i]);
+        d = st - (int)s.sgn[i];
+        if (d != 0) s.sgn[i] = (signed char)st;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, d != 0);
+      const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+      if (d != 0 && pos < kChgW) s.chg[warp * kChgW + pos] = (i << 2) | (d + 2);
+      cnt += __popc(m);
+    }
+    if (lane == 0) s.wcnt[warp] = cnt;
+    __syncthreads();
+    int over = 0;
+    for (int w = 0; w < W; ++w) over |= s.wcnt[w] > kChgW;
+    if (!over) {
+      // per-warp partial updates, lanes over columns
+      constexpr int kPc = kMaxP / 32;
+      float part[kPc];
+#pragma unroll
+      for (int u = 0; u < kPc; ++u) part[u] = 0.f;
+      const int m = min(s.wcnt[warp], kChgW);
+      for (int e = 0; e < m; ++e) {
+        const int code = s.chg[warp * kChgW + e];
+        const int i = code >> 2;
+        const float dl = (float)((code & 3) - 2);
+#pragma unroll
+        for (int u = 0; u < kPc; ++u) {
+          const int c = lane + 32 * u;
+          if (c < p) part[u] += dl * xval(s, c, i);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kPc; ++u) {
+        const int c = lane + 32 * u;
+        if (c < p) s.red2[warp * p + c] = part[u];
+      }
+      __syncthreads();
+      for (int c = tid; c < p; c += G) {
+        double g = s.gd[c];
+        for (int w = 0; w < W; ++w) g -= (double)s.red2[w * p + c];
+        s.gd[c] = g;
+      }
+      __syncthreads();
+      for (int e = tid; e < W * p; e += G) s.red2[e] = e < p ? (float)s.gd[e] : 0.f;
+      __syncthreads();
+      return;
+    }
+    // too many changes: the full sums below (signs re-recorded there)
+  }
+  for (int c = 0; c < p; ++c) {
+    const float* __restrict__ col = colptr(s, c);
+    float a = 0.f, comp = 0.f;
+    for (int i0 = 0; i0 < n; i0 += G * kRowU<G>) {
+      float xv[kRowU<G>];
+#pragma unroll
+      for (int u = 0; u < kRowU<G>; ++u) {
+        const int i = i0 + u * G + tid;
+        xv[u] = i < n ? col[i] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kRowU<G>; ++u) {
+        const int i = i0 + u * G + tid;
+        if (i < n && !((s.mask[i >> 5] >> (i & 31)) & 1u)) {
+          const float t = -fsign(s.rr[i]) * xv[u] - comp;
+          const float nb = a + t;
+          comp = (nb - a) - t;
+          a = nb;
+        }
+      }
+    }
+    a = warp_sum(a) - warp_sum(comp);
+    if (lane == 0) s.red2[warp * p + c] = a;
+  }
+  for (int i = tid; i < n; i += G) {
+    const bool inb = (s.mask[i >> 5] >> (i & 31)) & 1u;
+    s.sgn[i] = (signed char)(inb ? 0 : (int)fsign(s.rr[i]));
+  }
+  __syncthreads();
+  for (int c = tid; c < p; c += G) {
+    double g = 0.0;
+    for (int w = 0; w < W; ++w) g += (double)s.red2[w * p + c];
+    s.gd[c] = g;
+  }
+  __syncthreads();
+  for (int e = tid; e < W * p; e += G) s.red2[e] = e < p ? (float)s.gd[e] : 0.f;
+  __syncthreads();
+}
+
 __device__ __forceinline__ unsigned mix32(unsigned x) {
   x *= 0x9E3779B1u;
   x ^= x >> 16;
@@ -1665,7 +1766,8 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     // column sums g_c = -sum_{rows not in basis} sign(r_i) x_ic (loads
     // batched kRowU<G> per thread; per-thread order is row order, compensated
     // summation: at n = 2e4 plain float sums err by ~1e-3 relative)
-    for (int c = 0; c < p; ++c) {
+    if (G > 32) colsums_blk<G>(s, it == 0);
+    else for (int c = 0; c < p; ++c) {
       const float* __restrict__ col = colptr(s, c);
       float a = 0.f, comp = 0.f;
       for (int i0 = 0; i0 < n; i0 += G * kRowU<G>) {
@@ -1719,11 +1821,10 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
       float* vd = G == 32 ? s.cb[0] : s.vdg;
       edge_products<G>(s, vd);
       gsync<G>();
-      if (tid == 0) s.vd = vd;
+      if (tid == 0) { s.colp = vd; s.pbase = 0.f; s.pq = s.qcode; }
       gsync<G>();
-      if (G == 32) select_fused<kEdge>(s, 0.f, false, 0.f, 0.f);
-      else select_fused_blk<G, kEdge>(s, 0.f, false, 0.f, 0.f);
-      if (tid == 0) s.vd = nullptr;
+      if (G == 32) select_fused(s, 0.f, false, 0.f, 0.f);
+      else select_fused_blk<G>(s, 0.f, false, 0.f, 0.f);
       gsync<G>();
     }
     const float ts = s.zstar;
@@ -1979,6 +2080,7 @@ __host__ __device__ size_t group_smem_bytes(int ncap, int P) {
   size_t words = (size_t)ncap + colbuf + sel_bm + 7 * (size_t)P + (size_t)W * P +
                  9 * (size_t)P + 3 * ((size_t)P + 1) + (size_t)ncap / 32 + 1 +
                  2 * (size_t)W * 16 + 64 + W + kHist;
+  if (G > 32) words += ((size_t)ncap + 3) / 4 + 2 * (size_t)P + 2 + (size_t)W * kChgW;
   return ((words * 4 + 15) / 16) * 16;
 }
 
@@ -1987,8 +2089,9 @@ __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   constexpr int W = G / 32;
   s.cap = G == 32 ? kBufCap : W * kSubCap;
   s.maskw = ncap / 32 + 1;
-  s.vd = nullptr;
   s.vdg = nullptr;
+  s.pq = -1;
+  s.pbase = 0.f;
   float* f = reinterpret_cast<float*>(raw);
   s.rr = f; f += ncap;
   if (G == 32) { s.cb[0] = f; f += ncap; s.cb[1] = f; f += ncap; }
@@ -2022,6 +2125,13 @@ __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   s.sampw = f; f += 32;
   s.wcnt = reinterpret_cast<int*>(f); f += W;
   s.bhist = reinterpret_cast<unsigned*>(f); f += kHist;
+  s.sgn = nullptr; s.gd = nullptr; s.chg = nullptr;
+  if (G > 32) {
+    s.chg = reinterpret_cast<int*>(f); f += W * kChgW;
+    if ((reinterpret_cast<uintptr_t>(f) & 7u) != 0) f += 1;  // 8-byte alignment
+    s.gd = reinterpret_cast<double*>(f); f += 2 * P;
+    s.sgn = reinterpret_cast<signed char*>(f); f += (ncap + 3) / 4;
+  }
 }
 
 template <int G, int NW>
