@@ -51,6 +51,9 @@ def parse():
                     help="skip the 20000 x 128 block-per-fit measurement")
     ap.add_argument("--large-problems", type=int, default=256)
     ap.add_argument("--no-tune", action="store_true", help="library's default launch shape")
+    ap.add_argument("--launch", default=None,
+                    help="fixed launch shape GxF/oW (threads per fit, fits per block, work "
+                         "order), e.g. 32x3/o0; skips the autotuner")
     return ap.parse_args()
 
 
@@ -162,10 +165,10 @@ def log(*a):
     print("[bench]", *a, file=sys.stderr, flush=True)
 
 
-def profile_traffic(name: str, source: str):
+def profile_traffic(name: str, source: str, launch_tag: str | None):
     """DRAM bytes per launch recorded in profiles/<name> by an ncu capture,
     if it was taken on the current source of the kernel (its SHA-256 is
-    recorded beside the number); None otherwise."""
+    recorded beside the number) with the same launch shape; None otherwise."""
     try:
         text = open(os.path.join(ROOT, "profiles", name)).read()
         cur = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
@@ -173,7 +176,8 @@ def profile_traffic(name: str, source: str):
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
-    if not m or not h or h.group(1) != cur:
+    t = re.search(r"launch_shape:\s*(\S+)", text)
+    if not m or not h or h.group(1) != cur or not t or t.group(1) != launch_tag:
         return None
     return float(m.group(1))
 
@@ -212,7 +216,11 @@ def main():
 
     # launch shape: autotuned on every 2nd problem (outside the timed region)
     launch, tuned = None, {}
-    if not args.no_tune:
+    if args.launch:
+        g_, rest = args.launch.split("x")
+        f_, o_ = rest.split("/o")
+        launch = ll.Launch(int(g_), int(f_), int(o_))
+    elif not args.no_tune:
         from paper_2510_15649_gb300 import tune
         lam0 = ll.lambda_path(ll.lambda_max(pr, ws), L, 1e-3)
         # the sample must outnumber the resident fits (~1000) so that it
@@ -356,8 +364,10 @@ def main():
     peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x clock
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak,
-                        "traffic": profile_traffic("launches_batched4096.md",
-                                                   "paper_2510_15649_gb300/csrc/fit_block.cu"),
+                        "traffic": profile_traffic(
+                            "launches_batched4096.md", "paper_2510_15649_gb300/csrc/fit_block.cu",
+                            None if launch is None else
+                            f"{launch.group_threads}x{launch.fits_per_block}/o{launch.work_order}"),
                         "kernel": "fit_block_kernel", "kernel_ms": 1e3 * t_fit,
                         "row_updates_per_launch": ru}
     line["clocks"] = clk_s

@@ -112,7 +112,11 @@ void ladlasso_default_opts(ladlasso_opts* o);
  *            (row slot index i >= 0, or -(j+1) for b_j = 0); consumed by
  *            ladlasso_fit_backward
  * counters   [B*L*8] device or NULL: sweeps, chop probes, polish steps,
- *            flags (1: CCD point optimal, 2: chop ran, 4: chop point optimal),
+ *            flags (1: CCD point optimal, 2: chop ran, 4: chop point optimal;
+ *            bits 3-5, batched kernel: how the pivoting polish ended, 0
+ *            optimal, 1 basis cycle accepted as a degenerate optimum, 2 basis
+ *            cycle with violations left, 3 pivot cap, 4 singular basis,
+ *            5 flat edge),
  *            selection passes over the rows, 1-D selections, kilocycles in
  *            descent + chop, kilocycles in basis/polish work (the last four
  *            are counted by the batched kernel only, else 0)

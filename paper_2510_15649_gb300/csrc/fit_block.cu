@@ -54,7 +54,7 @@ constexpr int kMaxPasses = 64; // cap on fused passes per 1-D step
 constexpr int kSubCap = 128;   // block path: selection sub-buffer per warp
 constexpr int kBlockG = 512;   // block path: threads per fit
 constexpr int kHist = 32;               // polish: bases remembered for cycle detection
-constexpr int kChgW = 64;               // block polish: changed rows per warp before a full recompute
+constexpr int kChgW = 256;              // block polish: changed rows per warp before a full recompute
 constexpr float kStallTolFactor = 50.f; // cycling vertex accepted when violations are below this x tol
 
 // Uniform per-group state, resident in shared memory.
@@ -72,7 +72,7 @@ struct St {
   // block path, incremental column sums of the polish:
   signed char* sgn;                // [ncap] sign of row i in the last sums (0 in basis)
   double* gd;                      // [P] g_c = -sum_i sgn_i x_ic
-  int* chg;                        // [W * kChgW] changed rows, packed (i << 2) | (delta + 2)
+  int* chg;                        // [W * kChgW] changed rows, packed (i << 3) | (delta + 2)
   float* sk; float* sw; int* sid;      // special breakpoints [P+1]
   unsigned* mask;                      // basis-row bitmap [maskw]
   float* redf; int* redi;              // reductions [W*16]
@@ -94,6 +94,7 @@ struct St {
   // broadcast slots
   float lo, hi, acc, wpart, half, zstar, above;
   int part, m, owner, q, flag, iter, first, has_prev, bland;
+  int pexit;    // how the last polish ended (see polish)
   float worst;  // largest multiplier violation at the last test
   // fused-pass results
   float p_wl, p_wi, p_wt, p_amin;
@@ -1626,7 +1627,8 @@ __device__ __noinline__ void colsums_blk(St& s, bool full) {
       }
       const unsigned m = __ballot_sync(0xffffffffu, d != 0);
       const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-      if (d != 0 && pos < kChgW) s.chg[warp * kChgW + pos] = (i << 2) | (d + 2);
+      // delta in [-2, 2] (a sign flip is 2): three bits
+      if (d != 0 && pos < kChgW) s.chg[warp * kChgW + pos] = (i << 3) | (d + 2);
       cnt += __popc(m);
     }
     if (lane == 0) s.wcnt[warp] = cnt;
@@ -1640,10 +1642,11 @@ __device__ __noinline__ void colsums_blk(St& s, bool full) {
 #pragma unroll
       for (int u = 0; u < kPc; ++u) part[u] = 0.f;
       const int m = min(s.wcnt[warp], kChgW);
+#pragma unroll 4
       for (int e = 0; e < m; ++e) {
         const int code = s.chg[warp * kChgW + e];
-        const int i = code >> 2;
-        const float dl = (float)((code & 3) - 2);
+        const int i = code >> 3;
+        const float dl = (float)((code & 7) - 2);
 #pragma unroll
         for (int u = 0; u < kPc; ++u) {
           const int c = lane + 32 * u;
@@ -1742,6 +1745,9 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
   const int tid = gtid<G>(), lane = lane_id(), warp = gwarp<G>();
   const int n = s.n, p = s.p;
   int it = 0, nh = 0, cycled = 0;  // nh: bases hashed so far
+  // exit: 0 optimal, 1 cycle accepted, 2 cycle rejected, 3 pivot cap,
+  // 4 singular basis, 5 flat edge
+  int exit_code = 0;
   *is_opt = 0;
   *nonunique = 0;
   if (tid == 0) s.bland = 0;
@@ -1755,7 +1761,7 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
   for (;;) {
     snap_g<G>(s);
     gsync<G>();
-    if (!s.flag) break;  // singular basis: give up (status MAX_ITERS)
+    if (!s.flag) { exit_code = 4; break; }  // singular basis: give up (status MAX_ITERS)
     recompute_r<G>(s);
     for (int w = tid; w < s.maskw; w += G) s.mask[w] = 0u;
     gsync<G>();
@@ -1798,7 +1804,7 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     if (warp == 0) mult_pick(s, it < max_piv);
     gsync<G>();
     const int q = s.q;
-    if (q < 0) { *is_opt = 1; *nonunique = s.iter; break; }
+    if (q < 0) { *is_opt = 1; *nonunique = s.iter; exit_code = 0; break; }
     if (cycled) {
       // a basis repeated under Bland's rule: each iteration is a function
       // of the basis alone, so the polish would loop (float32 noise in the
@@ -1807,10 +1813,13 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
       if (s.worst <= kStallTolFactor * s.a->o.tol_opt * fmaxf(1.f, s.lam)) {
         *is_opt = 1;
         *nonunique = 1;
+        exit_code = 1;
+      } else {
+        exit_code = 2;
       }
       break;
     }
-    if (it >= max_piv) break;
+    if (it >= max_piv) { exit_code = max_piv > 0 ? 3 : 0; break; }
     // edge line search: breakpoints of t -> F(b + t d)
     if (tid == 0) {
       s.qcode = s.code[q];
@@ -1829,7 +1838,7 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     }
     const float ts = s.zstar;
     const int own = s.owner;
-    if (own == kNone) break;  // flat along the edge (cannot happen when F decreases)
+    if (own == kNone) { exit_code = 5; break; }  // flat along the edge (cannot happen when F decreases)
     if (warp == 0) {
       for (int c = lane; c < p; c += 32) s.bv[c] += ts * s.dv[c];
       __syncwarp();
@@ -1854,6 +1863,8 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     if (tid == 0 && rep_seen) s.bland = 1;
     ++it;
   }
+  gsync<G>();
+  if (tid == 0) s.pexit = exit_code;
   gsync<G>();
   return it;
 }
@@ -2043,6 +2054,7 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
       choose_polish_start<G>(s);
       const int mp = A.o.max_pivots > 0 ? A.o.max_pivots : 4 * p + 64;
       pivots = polish<G>(s, mp, &is_opt, &nonu);
+      flags |= s.pexit << 3;
       if (!is_opt) status |= kFitMaxIters;
     }
     if (is_opt) {  // warm start for the next path position's polish
