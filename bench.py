@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 20000 x 128 block-per-fit measurement")
     ap.add_argument("--large-problems", type=int, default=256)
+    ap.add_argument("--large-lambdas", type=int, default=32)
+    ap.add_argument("--no-diff", action="store_true",
+                    help="skip the forward + adjoint measurement (512 x 400/100 x 16)")
     ap.add_argument("--no-tune", action="store_true", help="library's default launch shape")
     ap.add_argument("--launch", default=None,
                     help="fixed launch shape GxF/oW (threads per fit, fits per block, work "
@@ -380,8 +383,9 @@ def main():
             big = synth.large(B=Bl)
             pb = ll.Problems.from_numpy(big, device=dev)
             del big
-            wsb = ll.workspace(pb, 32)
-            lamb = ll.lambda_path(ll.lambda_max(pb, wsb), 32, 1e-3)
+            wsb = ll.workspace(pb, args.large_lambdas)
+            Ll = args.large_lambdas
+            lamb = ll.lambda_path(ll.lambda_max(pb, wsb), Ll, 1e-3)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -403,7 +407,7 @@ def main():
                 pass
             cert = int(np.sum((sb & 3) == 0))
             line["large"] = {
-                "workload": f"{Bl} problems x 20000 rows x 128 columns, AR(1) 0.5, L=32",
+                "workload": f"{Bl} problems x 20000 rows x 128 columns, AR(1) 0.5, L={Ll}",
                 "fits_per_s": cert / tl, "kernel_ms": 1e3 * tl, "certified_fraction": cert / sb.size,
                 "launch": "one 512-thread block per fit",
                 "roofline": {"bound": "hbm", "achieved": byts / tl / 1e9, "peak": hbm_peak,
@@ -415,6 +419,39 @@ def main():
             torch.cuda.empty_cache()
         except Exception as ex:
             line["large"] = {"error": str(ex)}
+
+    # differentiation: forward fit at 0.1 lambda_max on the training rows and
+    # the adjoint of the validation LAD loss (one launch each)
+    if not args.no_diff and rank == 0:
+        try:
+            dd = synth.diff()
+            ptr = ll.Problems.from_numpy(dd["train"], device=dev)
+            pva = ll.Problems.from_numpy(dd["val"], device=dev)
+            Bd = ptr.B
+            wsd = ll.workspace(ptr, 1)
+            lamd = (0.1 * ll.lambda_max(ptr, wsd)).reshape(Bd, 1).contiguous()
+            up = torch.ones(Bd, device=dev)
+            fw = ll.fit(ptr, lamd, ws=wsd, basis=True)  # warm-up
+            ll.fit_backward(ptr, fw, 0, pva, up, ws=wsd)
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            fw = ll.fit(ptr, lamd, ws=wsd, basis=True)
+            ev[1].record(stream)
+            gb = ll.fit_backward(ptr, fw, 0, pva, up, ws=wsd)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            tf, tb = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+            sd = fw["status"].cpu().numpy()
+            gs = gb["status"].cpu().numpy()
+            line["diff"] = {
+                "workload": "512 problems, 400 train / 100 validation rows, p=16, lambda=0.1 lambda_max",
+                "forward_fits_per_s": int(np.sum((sd & 3) == 0)) / tf, "forward_ms": 1e3 * tf,
+                "backward_ms": 1e3 * tb, "backward_problems_per_s": Bd / tb,
+                "strict_vertex_fraction": float(np.mean(gs == 0))}
+            log(f"diff {line['diff']}")
+        except Exception as ex:
+            line["diff"] = {"error": str(ex)}
 
     # thread-per-fit comparison: the paper's one-fit-per-thread layout is far
     # too slow for the full workload inside a bench run, so both kernels are
