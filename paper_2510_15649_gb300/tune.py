@@ -57,8 +57,11 @@ def _subset(pr: ll.Problems, lambdas: torch.Tensor, every: int):
 
 
 def autotune(pr: ll.Problems, lambdas: torch.Tensor, *, opts: ll.Opts | None = None,
-             sample_problems: int = 512, repeats: int = 2, use_cache: bool = True) -> tuple:
-    """Fastest launch shape for fitting `pr` along `lambdas`.
+             sample_problems: int = 512, repeats: int = 2, use_cache: bool = True,
+             tie: float = 0.01) -> tuple:
+    """Fastest launch shape for fitting `pr` along `lambdas`; among shapes
+    within `tie` (relative) of the fastest, the one-warp shape with the fewest
+    fits per block (smaller instruction-cache and L2 footprint per SM).
     Returns (Launch, {shape: seconds})."""
     L = int(lambdas.reshape(pr.B, -1).shape[1])
     dev = pr.X.device
@@ -85,6 +88,8 @@ def autotune(pr: ll.Problems, lambdas: torch.Tensor, *, opts: ll.Opts | None = N
             e1.synchronize()
             best = min(best, e0.elapsed_time(e1) / 1e3)
         times[c] = best
-    choice = min(times, key=times.get)
+    best = min(times.values())
+    near = [c for c, t in times.items() if t <= best * (1.0 + tie)]
+    choice = min(near, key=lambda c: (c.group_threads != 32, c.fits_per_block, c.work_order))
     _cache[key] = (choice, times)
     return choice, times
