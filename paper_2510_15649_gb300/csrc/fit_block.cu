@@ -26,7 +26,7 @@
 // classifies it against a window [lo, hi] (weight below, weight inside,
 // count inside) and compacts only the keys inside into a small shared
 // buffer.  The window for an axis step is centred on the current b_j with
-// the width of that axis' last move, so near convergence one pass holding a
+// a half-width of four times that axis' last move, so near convergence one pass holding a
 // handful of keys decides the step.  A miss shrinks the open interval known
 // to hold z* and draws the next window from 32 sampled keys in it; every
 // pass either finishes or strictly shrinks that interval.  Sums are per-lane
@@ -37,8 +37,19 @@ namespace ll {
 namespace {
 
 constexpr float kInf = INFINITY;
-constexpr int kSampM = 3;      // bracket half-width (samples) on buffer levels
-constexpr int kWinM = 4;       // bracket half-width (samples) for pass windows
+#ifndef LL_SAMPM
+#define LL_SAMPM 3
+#endif
+#ifndef LL_WINM
+#define LL_WINM 2
+#endif
+#ifndef LL_DLF
+#define LL_DLF 4.f
+#endif
+constexpr int kSampM = LL_SAMPM;  // bracket half-width (samples) on buffer levels
+constexpr int kWinM = LL_WINM;    // bracket half-width (samples) for pass windows
+constexpr float kDlf = LL_DLF;    // axis window half-width, times the axis' last move
+                                  // (4, with 2-sample pass brackets, measured best on the bench mix)
 #ifndef LL_KU
 #define LL_KU 1
 #endif
@@ -1481,7 +1492,7 @@ __device__ __noinline__ float axis_update(St& s, int j, int jnext) {
   if (gtid<G>() == 0) {
     s.bv[j] = z;
     s.piv[j] = own == kNone ? -2 : (own < 0 ? -1 : own);
-    s.dl[j] = fmaxf(2.f * fabsf(d), 1e-5f * fmaxf(1.f, fabsf(z)));
+    s.dl[j] = fmaxf(kDlf * fabsf(d), 1e-5f * fmaxf(1.f, fabsf(z)));
     if (G == 32) s.cur ^= 1;
   }
   gsync<G>();
