@@ -403,6 +403,17 @@ def main():
                         "kernel": "fit_block_kernel", "kernel_ms": 1e3 * t_fit,
                         "row_updates_per_launch": ru}
     line["clocks"] = clk_s
+    # per-fit counters of the last timed step (work the method did)
+    def pct(a):
+        return {"mean": float(np.mean(a)), "p50": float(np.percentile(a, 50)),
+                "p99": float(np.percentile(a, 99)), "max": float(np.max(a))}
+    fl = cnt[..., 3]
+    line["counters"] = {"sweeps": pct(cnt[..., 0]), "chop_probes": pct(cnt[..., 1]),
+                        "polish_pivots": pct(cnt[..., 2]),
+                        "selection_passes_per_select": float(cnt[..., 4].sum() / max(1, cnt[..., 5].sum())),
+                        "ccd_point_optimal": float(np.mean((fl & 1) != 0)),
+                        "chop_ran": float(np.mean((fl & 2) != 0)),
+                        "chop_point_optimal": float(np.mean((fl & 4) != 0))}
 
     # long problems: 20000 x 128 per fit, one 512-thread block per fit,
     # columns streamed from HBM (one launch, timed with events)

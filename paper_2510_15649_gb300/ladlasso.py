@@ -103,6 +103,27 @@ def default_opts(**kw) -> Opts:
     return o
 
 
+class _nvtx:
+    """NVTX range around one library call (visible in profilers' timelines;
+    a no-op where NVTX is unavailable)."""
+
+    def __init__(self, name: str):
+        self.name = name
+        self.on = False
+
+    def __enter__(self):
+        try:
+            torch.cuda.nvtx.range_push(self.name)
+            self.on = True
+        except Exception:
+            pass
+        return self
+
+    def __exit__(self, *a):
+        if self.on:
+            torch.cuda.nvtx.range_pop()
+
+
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
@@ -179,8 +200,9 @@ def lambda_max(pr: Problems, ws: torch.Tensor | None = None, stream=None) -> tor
     ws = workspace(pr) if ws is None else ws
     out = torch.empty(pr.B, dtype=torch.float32, device=pr.X.device)
     d = pr.dims(1, ws)
-    _check(lib().ladlasso_lambda_max(_ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets),
-                                     C.byref(d), _ptr(out), _stream(stream)))
+    with _nvtx("ladlasso_lambda_max"):
+        _check(lib().ladlasso_lambda_max(_ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx),
+                                         _ptr(pr.offsets), C.byref(d), _ptr(out), _stream(stream)))
     return out
 
 
@@ -239,8 +261,9 @@ def fit(pr: Problems, lambdas: torch.Tensor, *, b_init=None, opts: Opts | None =
         d.group_threads, d.fits_per_block = launch.group_threads, launch.fits_per_block
         d.work_order = launch.work_order
     fn = lib().ladlasso_fit_batched_thread if per_thread else lib().ladlasso_fit_batched
-    _check(fn(_ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), _ptr(lam.contiguous()),
-              _ptr(out["b"]), _ptr(out["obj"]), C.byref(d), _stream(stream)))
+    with _nvtx("ladlasso_fit_batched_thread" if per_thread else "ladlasso_fit_batched"):
+        _check(fn(_ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), _ptr(lam.contiguous()),
+                  _ptr(out["b"]), _ptr(out["obj"]), C.byref(d), _stream(stream)))
     return out
 
 
@@ -292,13 +315,14 @@ def fit_backward(pr: Problems, fwd: dict, pos: int, val: Problems, grad_up: torc
              status=torch.empty(B, dtype=torch.int32, device=dev),
              loss=torch.empty(B, dtype=torch.float32, device=dev))
     d = pr.dims(L, ws, opts)
-    _check(lib().ladlasso_fit_backward(
-        _ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), C.byref(d), int(pos),
-        _ptr(fwd["b"]), _ptr(fwd["basis"]), _ptr(val.X), int(val.X.stride(0)), _ptr(val.y),
-        _ptr(val.row_idx), _ptr(val.offsets), int(val.y.numel()),
-        _ptr(grad_up.contiguous().float()),
-        _ptr(g["lam"]), _ptr(g["y"]), _ptr(g["X"]), _ptr(g["yv"]), _ptr(g["Xv"]),
-        _ptr(g["status"]), _ptr(g["loss"]), _stream(stream)))
+    up = grad_up.contiguous().float()
+    with _nvtx("ladlasso_fit_backward"):
+        _check(lib().ladlasso_fit_backward(
+            _ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), C.byref(d), int(pos),
+            _ptr(fwd["b"]), _ptr(fwd["basis"]), _ptr(val.X), int(val.X.stride(0)), _ptr(val.y),
+            _ptr(val.row_idx), _ptr(val.offsets), int(val.y.numel()), _ptr(up),
+            _ptr(g["lam"]), _ptr(g["y"]), _ptr(g["X"]), _ptr(g["yv"]), _ptr(g["Xv"]),
+            _ptr(g["status"]), _ptr(g["loss"]), _stream(stream)))
     return g
 
 

@@ -21,6 +21,34 @@ from . import ladlasso as ll
 _cache: dict = {}
 
 
+def save_cache(path: str) -> None:
+    """Write the autotuner's choices (per device and problem-set signature)
+    to a JSON file."""
+    import json
+    rows = [{"key": list(k), "choice": [c.group_threads, c.fits_per_block, c.work_order],
+             "seconds": {f"{x.group_threads}x{x.fits_per_block}/o{x.work_order}": t
+                         for x, t in times.items()}}
+            for k, (c, times) in _cache.items()]
+    with open(path, "w") as f:
+        json.dump(rows, f, indent=1)
+
+
+def load_cache(path: str) -> int:
+    """Read choices written by save_cache; returns how many were loaded."""
+    import json
+    with open(path) as f:
+        rows = json.load(f)
+    for r in rows:
+        g, fb, o = r["choice"]
+        times = {}
+        for tag, t in r.get("seconds", {}).items():
+            gs, rest = tag.split("x")
+            fs, os_ = rest.split("/o")
+            times[ll.Launch(int(gs), int(fs), int(os_))] = float(t)
+        _cache[tuple(r["key"])] = (ll.Launch(g, fb, o), times)
+    return len(rows)
+
+
 def candidates(pr: ll.Problems) -> list:
     """Launch shapes the library accepts for `pr`."""
     out = []

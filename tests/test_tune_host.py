@@ -27,3 +27,17 @@ def test_long_problems_only_get_the_block_shape():
 
 def test_no_candidate_beyond_every_shape():
     assert tune.candidates(Pr(128, 10 ** 6)) == []
+
+
+def test_cache_round_trips_through_json(tmp_path):
+    tune._cache.clear()
+    key = ("GB300", 32, 2000, 4096, 16, False)
+    times = {ll.Launch(32, 3, 0): 1.046, ll.Launch(32, 5, 1): 1.107, ll.Launch(512, 0, 0): 2.0}
+    tune._cache[key] = (ll.Launch(32, 3, 0), times)
+    path = str(tmp_path / "tune.json")
+    tune.save_cache(path)
+    tune._cache.clear()
+    assert tune.load_cache(path) == 1
+    choice, t2 = tune._cache[key]
+    assert choice == ll.Launch(32, 3, 0) and t2 == times
+    tune._cache.clear()
