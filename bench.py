@@ -173,14 +173,19 @@ def log(*a):
 def profile_traffic(name: str, source: str, launch_tag: str | None):
     """DRAM bytes per launch recorded in profiles/<name> by an ncu capture
     (lines `traffic_bytes_per_launch[<shape>]: <bytes>`), if it was taken on
-    the current source of the kernel (its SHA-256 is recorded beside the
-    numbers) with the same launch shape; None otherwise."""
+    the current code of the kernel (the SHA-256 of its source without
+    comments is recorded beside the numbers) with the same launch shape;
+    None otherwise."""
     try:
         text = open(os.path.join(ROOT, "profiles", name)).read()
-        cur = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+        # the code of the kernel source: `//` comments, trailing blanks and
+        # empty lines removed, so comment edits keep a capture valid
+        code = [re.sub(r"//.*$", "", ln).rstrip()
+                for ln in open(os.path.join(ROOT, source)).read().split("\n")]
+        cur = hashlib.sha256("\n".join(ln for ln in code if ln.strip()).encode()).hexdigest()
     except OSError:
         return None
-    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", text)
+    h = re.search(r"kernel_code_sha256:\s*([0-9a-f]{64})", text)
     if not h or h.group(1) != cur or launch_tag is None:
         return None
     m = re.search(r"traffic_bytes_per_launch\[" + re.escape(launch_tag) + r"\]:\s*([0-9.eE+]+)", text)

@@ -2,14 +2,16 @@
 // time and takes problems from a device work queue (persistent grid).
 //   G = 32   one warp per fit, NW independent warps per block, no block
 //            barriers; each 1-D step is one fused pass over the rows (below)
-//   G > 32   one block per fit (long problems); keys staged in shared memory
-//            and narrowed level by level with block barriers
+//            reading the column from a shared-memory double buffer
+//   G > 32   one block per fit (long problems): the same windowed passes,
+//            the warps classifying interleaved row chunks into per-warp
+//            sub-buffers, the columns streamed from the gathered design
 //
 // Per fit:
-//   shared   residual r (n floats), a selection buffer of breakpoints, the
+//   shared   residual r (n floats), selection buffers of breakpoints, the
 //            coefficient vector and the p x p basis algebra of the polish
 //   global   the problem's design gathered column-major (workspace), so a
-//            column read is one coalesced sweep (L2-resident per fit)
+//            column read is one coalesced sweep
 //
 // Method, per lambda of the path (paper, Sections 3.3-3.5):
 //   1. cyclical coordinate descent, each axis step the exact 1-D minimiser:
