@@ -154,3 +154,46 @@ def test_large_workload_sampled_certificates(ll):
         Fg = oracle.objective(Xq, yq, b[q, l], lam_h[q, l])
         assert ref["status"][0] & 1 == 0
         assert (Fg - ref["f"][0]) <= 1e-5 * max(1.0, ref["f"][0]), (q, l, Fg, ref["f"][0])
+
+
+def test_one_warp_path_at_its_row_limit(ll):
+    # n = 8192, the largest problem the one-warp path takes, p = 32
+    batch = synth.batched_like(2, 8192, 8192, 32, 32, R=9000, P=32, seed=37)
+    lam = _oracle_lams(batch, 2, 1e-1)
+    assert ll.launch_shape(ll.Problems.from_numpy(batch))[0] == 32
+    out = _run(ll, batch, lam)
+    res = compare(batch, lam, out["b"], out["obj"], out["status"])
+    assert not res["bad"], res["bad"][:10]
+
+
+def test_block_path_at_its_row_limit(ll):
+    # one problem with the most rows one block's shared memory holds at
+    # P = 128 (the library reports the limit); sampled positions checked by
+    # the oracle's certificate or, for degenerate vertices, by its method
+    import torch
+    pr0 = ll.Problems.from_numpy(synth.batched_like(1, 10, 10, 4, 4, R=10, P=128, seed=1))
+    pr0.n_max = 10 ** 9
+    _, _, rows = ll.launch_shape(pr0, ll.Launch(512, 0))
+    big = synth.large(B=1, n=rows, p=128, seed=5)
+    pr = ll.Problems.from_numpy(big)
+    assert pr.n_max == rows
+    lam = ll.lambda_path(ll.lambda_max(pr), 4, 1e-2)
+    out = ll.fit(pr, lam, basis=True)
+    torch.cuda.synchronize()
+    st = out["status"].cpu().numpy()[0]
+    b = out["b"].cpu().numpy()[0].astype(np.float64)
+    basis = out["basis"].cpu().numpy()[0]
+    lam_h = lam.cpu().numpy()[0].astype(np.float64)
+    X, y = big["X"].astype(np.float64), big["y"].astype(np.float64)
+    assert np.all((st & 2) == 0)
+    for l in (1, 3):
+        bv = _vertex(X, y, basis[l])
+        Fg = oracle.objective(X, y, b[l], lam_h[l])
+        if st[l] == 0:
+            gap, _ = oracle.certify(X, y, bv, lam_h[l])
+            Fv = oracle.objective(X, y, bv, lam_h[l])
+            assert gap <= 1e-7 * max(1.0, Fv), (l, gap, Fv)
+            assert abs(Fg - Fv) <= 1e-5 * max(1.0, Fv)
+        else:
+            ref = oracle.fit_path(X, y, [lam_h[l]], b_init=bv)
+            assert (Fg - ref["f"][0]) <= 1e-5 * max(1.0, ref["f"][0])
