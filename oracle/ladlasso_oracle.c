@@ -25,7 +25,10 @@
  *     orc_chop         ternary search along one axis over the locus of
  *                      axis-wise minima, each probe a coordinate descent
  *                      restricted to the other axes (Sections 3.4-3.5),
- *                      with range extension (Section 3.5).
+ *                      with range extension (Section 3.5); option
+ *                      chop_sections = 4 reads the paper's undefined
+ *                      "quadrature" search (Sections 1, 5) as four equal
+ *                      sections probed at the three inner points.
  *     orc_polish       exact finish: vertex-to-vertex edge line searches
  *                      (each itself a weighted median) until the
  *                      optimality multipliers certify the vertex.  The
