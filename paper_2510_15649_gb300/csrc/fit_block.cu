@@ -1613,7 +1613,7 @@ __device__ __noinline__ void chop(St& s, int k, int& sweeps, int& probes) {
   gsync<G>();
 }
 
-// (all G threads, block path) the polish's column sums
+// (all G threads) the polish's column sums
 //   g_c = -sum_{rows not in basis} sign(r_i) x_ic
 // into red2 (warp 0's slot; the others 0).  `full`: every column over every
 // row (compensated float sums per thread, FP64 across warps), remembering
@@ -1622,7 +1622,7 @@ __device__ __noinline__ void chop(St& s, int k, int& sweeps, int& probes) {
 // n = 2e4 the full sums are 2.6 M loads per pivot, the changes typically a
 // few hundred.  More than kChgW changed rows in some warp falls back to full.
 template <int G>
-__device__ __noinline__ void colsums_blk(St& s, bool full) {
+__device__ __noinline__ void colsums(St& s, bool full) {
   constexpr int W = G / 32;
   const int tid = gtid<G>(), lane = lane_id(), warp = gwarp<G>();
   const int n = s.n, p = s.p;
@@ -1645,7 +1645,7 @@ __device__ __noinline__ void colsums_blk(St& s, bool full) {
       cnt += __popc(m);
     }
     if (lane == 0) s.wcnt[warp] = cnt;
-    __syncthreads();
+    gsync<G>();
     int over = 0;
     for (int w = 0; w < W; ++w) over |= s.wcnt[w] > kChgW;
     if (!over) {
@@ -1671,15 +1671,15 @@ __device__ __noinline__ void colsums_blk(St& s, bool full) {
         const int c = lane + 32 * u;
         if (c < p) s.red2[warp * p + c] = part[u];
       }
-      __syncthreads();
+      gsync<G>();
       for (int c = tid; c < p; c += G) {
         double g = s.gd[c];
         for (int w = 0; w < W; ++w) g -= (double)s.red2[w * p + c];
         s.gd[c] = g;
       }
-      __syncthreads();
+      gsync<G>();
       for (int e = tid; e < W * p; e += G) s.red2[e] = e < p ? (float)s.gd[e] : 0.f;
-      __syncthreads();
+      gsync<G>();
       return;
     }
     // too many changes: the full sums below (signs re-recorded there)
@@ -1712,15 +1712,15 @@ __device__ __noinline__ void colsums_blk(St& s, bool full) {
     const bool inb = (s.mask[i >> 5] >> (i & 31)) & 1u;
     s.sgn[i] = (signed char)(inb ? 0 : (int)fsign(s.rr[i]));
   }
-  __syncthreads();
+  gsync<G>();
   for (int c = tid; c < p; c += G) {
     double g = 0.0;
     for (int w = 0; w < W; ++w) g += (double)s.red2[w * p + c];
     s.gd[c] = g;
   }
-  __syncthreads();
+  gsync<G>();
   for (int e = tid; e < W * p; e += G) s.red2[e] = e < p ? (float)s.gd[e] : 0.f;
-  __syncthreads();
+  gsync<G>();
 }
 
 __device__ __forceinline__ unsigned mix32(unsigned x) {
@@ -1756,7 +1756,7 @@ __device__ __noinline__ void basis_seen(St& s, int nh) {
 template <int G>
 __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonunique) {
   const int tid = gtid<G>(), lane = lane_id(), warp = gwarp<G>();
-  const int n = s.n, p = s.p;
+  const int p = s.p;
   int it = 0, nh = 0, cycled = 0;  // nh: bases hashed so far
   // exit: 0 optimal, 1 cycle accepted, 2 cycle rejected, 3 pivot cap,
   // 4 singular basis, 5 flat edge
@@ -1782,34 +1782,9 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
       for (int k = 0; k < p; ++k)
         if (s.code[k] >= 0) s.mask[s.code[k] >> 5] |= 1u << (s.code[k] & 31);
     gsync<G>();
-    // column sums g_c = -sum_{rows not in basis} sign(r_i) x_ic (loads
-    // batched kRowU<G> per thread; per-thread order is row order, compensated
-    // summation: at n = 2e4 plain float sums err by ~1e-3 relative)
-    if (G > 32) colsums_blk<G>(s, it == 0);
-    else for (int c = 0; c < p; ++c) {
-      const float* __restrict__ col = colptr(s, c);
-      float a = 0.f, comp = 0.f;
-      for (int i0 = 0; i0 < n; i0 += G * kRowU<G>) {
-        float xv[kRowU<G>];
-#pragma unroll
-        for (int u = 0; u < kRowU<G>; ++u) {
-          const int i = i0 + u * G + tid;
-          xv[u] = i < n ? col[i] : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < kRowU<G>; ++u) {
-          const int i = i0 + u * G + tid;
-          if (i < n && !((s.mask[i >> 5] >> (i & 31)) & 1u)) {
-            const float t = -fsign(s.rr[i]) * xv[u] - comp;
-            const float nb = a + t;
-            comp = (nb - a) - t;
-            a = nb;
-          }
-        }
-      }
-      a = warp_sum(a) - warp_sum(comp);
-      if (lane == 0) s.red2[warp * p + c] = a;
-    }
+    // column sums g_c = -sum_{rows not in basis} sign(r_i) x_ic: in full at
+    // the first pivot, then from the rows that changed (colsums)
+    colsums<G>(s, it == 0);
     gsync<G>();
     if (warp == 0) mult_solve<G>(s);
     if (G == 32) refine(s, s.mu, s.hv, true);
@@ -2105,7 +2080,7 @@ __host__ __device__ size_t group_smem_bytes(int ncap, int P) {
   size_t words = (size_t)ncap + colbuf + sel_bm + 7 * (size_t)P + (size_t)W * P +
                  9 * (size_t)P + 3 * ((size_t)P + 1) + (size_t)ncap / 32 + 1 +
                  2 * (size_t)W * 16 + 64 + W + kHist;
-  if (G > 32) words += ((size_t)ncap + 3) / 4 + 2 * (size_t)P + 2 + (size_t)W * kChgW;
+  words += ((size_t)ncap + 3) / 4 + 2 * (size_t)P + 2 + (size_t)W * kChgW;
   return ((words * 4 + 15) / 16) * 16;
 }
 
@@ -2151,7 +2126,7 @@ __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   s.wcnt = reinterpret_cast<int*>(f); f += W;
   s.bhist = reinterpret_cast<unsigned*>(f); f += kHist;
   s.sgn = nullptr; s.gd = nullptr; s.chg = nullptr;
-  if (G > 32) {
+  {
     s.chg = reinterpret_cast<int*>(f); f += W * kChgW;
     if ((reinterpret_cast<uintptr_t>(f) & 7u) != 0) f += 1;  // 8-byte alignment
     s.gd = reinterpret_cast<double*>(f); f += 2 * P;
