@@ -270,7 +270,7 @@ def main():
             step, graph_note = eager_step, f"eager (capture failed: {ex})"
             torch.cuda.synchronize()
 
-    launches_per_step = 5  # 2 offset checks, lambda_max, lambda_path, fit
+    launches_per_step = 6  # 2 offset checks, lambda_max, lambda_path, work order, fit
     t0 = time.perf_counter()
     for _ in range(args.warmup):
         lam = step()
