@@ -32,6 +32,15 @@ import torch
 from . import ladlasso as ll
 
 
+def admission_offsets(slots: np.ndarray, cap: int, S: int) -> np.ndarray:
+    """Offsets of the problem set made of the given (sorted) slots of a pool
+    of S slots of cap rows: slot k starts at k * cap and the set ends at the
+    pool's row count S * cap, as the library requires of a problem set's
+    last offset."""
+    ss = np.asarray(slots, np.int64)
+    return np.append(ss * cap, np.int64(S) * cap)
+
+
 @dataclass
 class Result:
     rid: int
@@ -46,7 +55,8 @@ class Result:
 @dataclass
 class ServeStats:
     completed: int = 0
-    fits: int = 0
+    fits: int = 0          # fits with valid input (status without BAD_INPUT)
+    bad_fits: int = 0
     steps: int = 0
     wall: float = 0.0
     latencies: list = field(default_factory=list)
@@ -55,7 +65,7 @@ class ServeStats:
 
     def summary(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
-        return dict(requests=self.completed, fits=self.fits, steps=self.steps,
+        return dict(requests=self.completed, fits=self.fits, bad_fits=self.bad_fits, steps=self.steps,
                     seconds=self.wall, fits_per_s=self.fits / max(self.wall, 1e-9),
                     p50_ms=1e3 * float(np.percentile(lat, 50)),
                     p99_ms=1e3 * float(np.percentile(lat, 99)),
@@ -111,9 +121,12 @@ class Server:
             slots.append(s)
         self.n_rows.copy_(torch.from_numpy(self.h_n), non_blocking=True)
         self.p.copy_(torch.from_numpy(self.h_p), non_blocking=True)
-        # lambda_max and the path of the new requests, on the device
+        # lambda_max and the path of the new requests, on the device: the new
+        # slots as one problem set; a problem set's last offset must be the
+        # pool's row count, so the last new slot's range runs to the end of
+        # the pool (its n_rows still bounds the rows it uses)
         ss = np.array(sorted(slots), np.int64)
-        offs = torch.from_numpy(np.append(ss * self.cap, ss[-1] * self.cap + self.cap)).to(self.dev)
+        offs = torch.from_numpy(admission_offsets(ss, self.cap, self.S)).to(self.dev)
         sub = ll.Problems(X=self.X, y=self.y, offsets=offs,
                           p=torch.from_numpy(self.h_p[ss]).to(self.dev), P=self.P,
                           n_max=self.cap,
@@ -175,7 +188,9 @@ class Server:
             self.h_obj[active, pos] = oh[active]
             self.h_st[active, pos] = sh[active]
             self.h_pos[active] += 1
-            st.fits += len(active)
+            valid = (sh[active] & 2) == 0
+            st.fits += int(valid.sum())
+            st.bad_fits += int((~valid).sum())
             done = active[self.h_pos[active] >= self.L]
             tnow = time.perf_counter()
             for s in done:

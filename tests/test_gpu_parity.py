@@ -164,3 +164,23 @@ def test_four_section_chop_parity(ll, per_thread):
     c = out["counters"]
     ran = (c[..., 3] & 2) != 0
     assert ran.any()
+
+
+def test_iteration_caps_report_max_iters_and_keep_the_best_point(ll):
+    # one CCD sweep and one polish pivot: fits that needed more are flagged
+    # MAX_ITERS; their objective is never above the starting point's
+    batch = synth.batched_like(24, 100, 400, 4, 10, R=500, P=10, seed=17)
+    lam = _oracle_lams(batch, 2, 1e-2)
+    capped = _run(ll, batch, lam, opts=ll.default_opts(max_sweeps=1, max_pivots=1, chop=0))
+    full = _run(ll, batch, lam)
+    st = capped["status"]
+    assert np.mean((st & 1) != 0) > 0.5
+    assert np.all((st & 2) == 0)
+    lh = lam.astype(np.float64)
+    for q in range(24):
+        X, y = oracle.problem(batch, q)
+        p = X.shape[1]
+        f0 = oracle.objective(X, y, np.zeros(p), lh[q, 0])
+        fc = oracle.objective(X, y, capped["b"][q, 0, :p].astype(np.float64), lh[q, 0])
+        ff = oracle.objective(X, y, full["b"][q, 0, :p].astype(np.float64), lh[q, 0])
+        assert fc <= f0 * (1 + 1e-6) and ff <= fc * (1 + 1e-6)

@@ -23,6 +23,9 @@ def test_served_results_equal_alone_fits():
     results, st = srv.run(trace, time_scale=1.0)
     assert st.completed == len(trace)
     assert st.max_active > 1 and st.steps >= 5
+    # every request was fitted on valid input (its own lambda path)
+    assert st.bad_fits == 0
+    assert all(np.all((r.status & 2) == 0) and np.all(np.isfinite(r.lambdas)) for r in results)
     summ = st.summary()
     assert summ["p99_ms"] >= summ["p50_ms"] > 0
     for r in results[:: max(1, len(results) // 12)]:
@@ -42,3 +45,33 @@ def test_served_results_equal_alone_fits():
         np.testing.assert_allclose(r.b, b, rtol=1e-5, atol=1e-6)
         np.testing.assert_allclose(r.obj, obj, rtol=1e-6)
         assert np.array_equal(r.b != 0, b != 0)
+
+
+def test_tight_memory_budget_queues_requests():
+    # a budget that holds about one request at a time: requests wait for
+    # memory instead of failing, and every one completes
+    from paper_2510_15649_gb300 import build
+    build.build()
+    from paper_2510_15649_gb300.serve import Server
+
+    trace = synth.serve_trace(rate=4000.0, seconds=0.005, seed=9, n_hi=300, p_hi=8)
+    assert len(trace) >= 8
+    budget = max(r["X"].shape[0] * r["X"].shape[1] for r in trace)
+    srv = Server(slots=8, cap=300, P=8, L=3, budget_floats=budget)
+    results, st = srv.run(trace, time_scale=1.0)
+    assert st.completed == len(trace)
+    assert st.queued_max >= 2
+    assert all(np.all((r.status & 2) == 0) for r in results)
+
+
+def test_request_beyond_slot_capacity_is_refused():
+    from paper_2510_15649_gb300 import build
+    build.build()
+    from paper_2510_15649_gb300.serve import Server
+
+    rng = np.random.default_rng(1)
+    big = dict(t=0.0, X=rng.standard_normal((400, 4)).astype(np.float32),
+               y=rng.standard_normal(400).astype(np.float32))
+    srv = Server(slots=2, cap=300, P=8, L=2)
+    with pytest.raises(ValueError):
+        srv.run([big])

@@ -66,3 +66,12 @@ def test_autotune_picks_a_candidate_and_caches(ll):
     assert all(t > 0 for t in times.values())
     again, _ = tune.autotune(pr, lam, sample_problems=32)
     assert again == choice
+
+
+def test_results_do_not_depend_on_work_order(ll):
+    import torch
+    batch, pr, lam = _setup(ll)
+    a = ll.fit(pr, lam, launch=ll.Launch(32, 0, 0))
+    b = ll.fit(pr, lam, launch=ll.Launch(32, 0, 1))
+    torch.cuda.synchronize()
+    assert torch.equal(a["b"], b["b"]) and torch.equal(a["obj"], b["obj"])
