@@ -29,7 +29,11 @@ sys.path.insert(0, ROOT)
 
 from paper_2510_15649_gb300 import synth  # noqa: E402
 
-WORKLOAD = "batched 4096 problems, shared X 2000x32, n~U[50,2000], p~U[4,32], L=16 (1e-3 path)"
+def workload(B: int, L: int) -> str:
+    """The batched workload's name with the problem and path sizes in use
+    (4096 and 16 by default)."""
+    return (f"batched {B} problems, shared X 2000x32, n~U[50,2000], p~U[4,32], "
+            f"L={L} (1e-3 path)")
 METRIC = "LAD-LASSO fits/s (certified, rel. obj err <= 1e-5 vs FP64 oracle)"
 
 
@@ -146,7 +150,7 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"{per_step} problems x {args.L} lambdas per step"},
+            "config": {"workload": workload(args.problems, args.L), "sample": f"{per_step} problems x {args.L} lambdas per step"},
             "cpu_baseline": {"value": v, "unit": "fits/s", "cores": used, "kind": "oracle",
                              "sample": f"{per_step} problems x {args.L} lambdas per step"},
             "e2e": {"value": v, "unit": "fits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -356,7 +360,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "problems_per_gpu": B, "lambdas": L,
+            "config": {"workload": workload(B, L), "problems_per_gpu": B, "lambdas": L,
                        "fits_per_gpu": fits, "l2": "flushed between timed steps (256 MB write)",
                        "step": graph_note,
                        "launch": None if launch is None else {
