@@ -70,14 +70,19 @@ extern "C" int ladlasso_fit_batched_noalloc(const float* X, const float* y, cons
   if (G == 0 || d->fits_per_block < 0 || d->work_order < 0 || d->work_order > 1)
     return LADLASSO_ERR_INVALID;
   if (d->n_max > fit_block_max_rows(G, d->P_cols)) return LADLASSO_ERR_NOMEM;
+  ladlasso_opts dflt;
+  ladlasso_default_opts(&dflt);
+  const ladlasso_opts* o = d->opts ? d->opts : &dflt;
+  if (!(o->tol_move >= 0.f && o->max_sweeps >= 1 && o->chop_bracket > 0.f &&
+        o->chop_tol >= 0.f && o->chop_max_probes >= 0 && o->chop_max_extend >= 0 &&
+        o->probe_max_sweeps >= 1 && o->max_pivots >= 0 && o->tol_opt >= 0.f &&
+        o->lambda_min_floor >= 0.f && (o->chop_sections == 3 || o->chop_sections == 4)))
+    return LADLASSO_ERR_INVALID;
   if (d->B == 0) return LADLASSO_OK;
   unsigned char* base = nullptr;
   int rc = scratch_for_current_device(&base);
   if (rc != LADLASSO_OK) return rc;
 
-  ladlasso_opts dflt;
-  ladlasso_default_opts(&dflt);
-  const ladlasso_opts* o = d->opts ? d->opts : &dflt;
   FitArgs a = {};
   a.X = X; a.y = y; a.row_idx = row_idx; a.offsets = offsets; a.p = d->p; a.n_rows = d->n_rows;
   a.lambdas = lambdas; a.b_init = d->b_init;
@@ -93,12 +98,6 @@ extern "C" int ladlasso_fit_batched_noalloc(const float* X, const float* y, cons
   a.o = {o->tol_move, o->max_sweeps, o->chop, o->chop_bracket, o->chop_tol, o->chop_max_probes,
          o->chop_max_extend, o->probe_max_sweeps, o->polish, o->max_pivots, o->tol_opt,
          o->lambda_min_floor, o->chop_sections};
-  if (!(a.o.tol_move >= 0.f && a.o.max_sweeps >= 1 && a.o.chop_bracket > 0.f &&
-        a.o.chop_tol >= 0.f && a.o.chop_max_probes >= 0 && a.o.chop_max_extend >= 0 &&
-        a.o.probe_max_sweeps >= 1 && a.o.max_pivots >= 0 && a.o.tol_opt >= 0.f &&
-        a.o.lambda_min_floor >= 0.f && (a.o.chop_sections == 3 || a.o.chop_sections == 4)))
-    return LADLASSO_ERR_INVALID;
-
   cudaStream_t st = (cudaStream_t)stream;
   int sms = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
