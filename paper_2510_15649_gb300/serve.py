@@ -166,7 +166,8 @@ class Server:
                 adm_ids.append(i)
                 extra += n * p
             if adm:
-                self._admit(adm, adm_ids)
+                with ll._nvtx("serve_admit"):
+                    self._admit(adm, adm_ids)
             active = np.nonzero(self.h_rid >= 0)[0]
             if len(active) == 0:
                 if nxt < len(trace):  # idle until the next arrival
@@ -176,13 +177,14 @@ class Server:
             lam = np.full(self.S, np.nan, np.float32)
             lam[active] = self.h_lam[active, self.h_pos[active]]
             self.lam_step.copy_(torch.from_numpy(lam).reshape(self.S, 1), non_blocking=True)
-            ll.fit(self.pr, self.lam_step, b_init=self.b, ws=self.ws, opts=self.opts,
-                   out=dict(b=self.b, obj=self.obj, status=self.status))
-            st.steps += 1
-            # every active request advanced one position; copy this step's results
-            bh = self.b.cpu().numpy()[:, 0]
-            oh = self.obj.cpu().numpy()[:, 0]
-            sh = self.status.cpu().numpy()[:, 0]
+            with ll._nvtx("serve_step"):
+                ll.fit(self.pr, self.lam_step, b_init=self.b, ws=self.ws, opts=self.opts,
+                       out=dict(b=self.b, obj=self.obj, status=self.status))
+                st.steps += 1
+                # every active request advanced one position; copy this step's results
+                bh = self.b.cpu().numpy()[:, 0]
+                oh = self.obj.cpu().numpy()[:, 0]
+                sh = self.status.cpu().numpy()[:, 0]
             pos = self.h_pos[active]
             self.h_b[active, pos] = bh[active]
             self.h_obj[active, pos] = oh[active]
