@@ -66,31 +66,43 @@ def _load():
     global _lib
     if _lib is None:
         build()
-        lib = C.CDLL(_LIB)
-        D, I, P = C.c_double, C.c_int, C.c_void_p
-        lib.orc_default_opts.argtypes = [C.POINTER(Opts)]
-        lib.orc_objective.restype = D
-        lib.orc_objective.argtypes = [I, I, P, P, P, D]
-        lib.orc_axis_update.restype = D
-        lib.orc_axis_update.argtypes = [I, I, P, P, P, D, I, C.POINTER(I), P]
-        lib.orc_ccd.restype = I
-        lib.orc_ccd.argtypes = [I, I, P, P, P, D, I, D, I, P, P]
-        lib.orc_fit_path.restype = None
-        lib.orc_fit_path.argtypes = [I, I, P, P, I, P, P, C.POINTER(Opts), P, P, P, P, P]
-        lib.orc_fit_batch.restype = I
-        lib.orc_fit_batch.argtypes = [I, P, P, P, P, P, P, I, I, P, C.POINTER(Opts), P, P, P, I]
-        lib.orc_lambda_max.restype = D
-        lib.orc_lambda_max.argtypes = [I, I, P, P]
-        lib.orc_brute_force.restype = D
-        lib.orc_brute_force.argtypes = [I, I, P, P, D, P, C.POINTER(I)]
-        lib.orc_simplex.restype = D
-        lib.orc_simplex.argtypes = [I, I, P, P, D, P, I]
-        lib.orc_certify.restype = D
-        lib.orc_certify.argtypes = [I, I, P, P, P, D, D, D, P]
-        lib.orc_grad.restype = I
-        lib.orc_grad.argtypes = [I, I, P, P, P, P, I, P, P, D, P, P, P, P, P]
-        _lib = lib
+        _lib = _bind(C.CDLL(_LIB))
     return _lib
+
+
+def use_library(path: str) -> None:
+    """Run every oracle function from the shared library at `path`, built
+    from a modified copy of ladlasso_oracle.c (the tests that plant a
+    mistake in the oracle to show that its pins catch it)."""
+    global _lib
+    _lib = _bind(C.CDLL(path))
+
+
+def _bind(lib):
+    """Declare the argument and result types of the C entry points."""
+    D, I, P = C.c_double, C.c_int, C.c_void_p
+    lib.orc_default_opts.argtypes = [C.POINTER(Opts)]
+    lib.orc_objective.restype = D
+    lib.orc_objective.argtypes = [I, I, P, P, P, D]
+    lib.orc_axis_update.restype = D
+    lib.orc_axis_update.argtypes = [I, I, P, P, P, D, I, C.POINTER(I), P]
+    lib.orc_ccd.restype = I
+    lib.orc_ccd.argtypes = [I, I, P, P, P, D, I, D, I, P, P]
+    lib.orc_fit_path.restype = None
+    lib.orc_fit_path.argtypes = [I, I, P, P, I, P, P, C.POINTER(Opts), P, P, P, P, P]
+    lib.orc_fit_batch.restype = I
+    lib.orc_fit_batch.argtypes = [I, P, P, P, P, P, P, I, I, P, C.POINTER(Opts), P, P, P, I]
+    lib.orc_lambda_max.restype = D
+    lib.orc_lambda_max.argtypes = [I, I, P, P]
+    lib.orc_brute_force.restype = D
+    lib.orc_brute_force.argtypes = [I, I, P, P, D, P, C.POINTER(I)]
+    lib.orc_simplex.restype = D
+    lib.orc_simplex.argtypes = [I, I, P, P, D, P, I]
+    lib.orc_certify.restype = D
+    lib.orc_certify.argtypes = [I, I, P, P, P, D, D, D, P]
+    lib.orc_grad.restype = I
+    lib.orc_grad.argtypes = [I, I, P, P, P, P, I, P, P, D, P, P, P, P, P]
+    return lib
 
 
 def _d(a):

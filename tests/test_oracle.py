@@ -373,6 +373,26 @@ def test_active_set_gradient_matches_finite_differences():
         yvp[v] += h
         fd = (np.abs(yvp - Xv @ r0["b"][0]).sum() - L0) / h
         assert abs(fd - g["gyv"][v]) < 1e-6
+    # validation design entries (direct terms): central differences, at
+    # rows whose residual does not change sign within the step
+    bb = r0["b"][0]
+    rv = yv - Xv @ bb
+    nchk = 0
+    for v in range(nv):
+        if abs(rv[v]) <= 2 * h * np.abs(bb).sum():
+            continue
+        for j in range(p):
+            Xp, Xm = Xv.copy(), Xv.copy()
+            Xp[v, j] += h
+            Xm[v, j] -= h
+            fd = (np.abs(yv - Xp @ bb).sum() - np.abs(yv - Xm @ bb).sum()) / (2 * h)
+            assert abs(fd - g["gXv"][v, j]) < 1e-6, (v, j, fd, g["gXv"][v, j])
+            nchk += 1
+    assert nchk >= p * nv // 2
+    # the upstream derivative scales every output
+    g2 = oracle.grad(X, y, bb, r0["basis"][0], Xv, yv, up=-2.5)
+    for k in ("gy", "gX", "gyv", "gXv"):
+        np.testing.assert_allclose(g2[k], -2.5 * g[k], rtol=1e-12, atol=1e-12)
     assert checked >= n // 2
 
 
