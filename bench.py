@@ -134,8 +134,8 @@ def run_reference(args, rank, world):
     times = []
     for s in range(args.warmup + args.steps):
         qs = np.arange(s * per_step, (s + 1) * per_step) % args.problems
-        lams = np.array(lm[s * per_step:(s + 1) * per_step])[:, None] * \
-            1e-3 ** (np.arange(args.L) / (args.L - 1))[None, :]
+        expo = np.arange(args.L) / max(1, args.L - 1)  # lambda_max down to 1e-3 lambda_max
+        lams = np.array(lm[s * per_step:(s + 1) * per_step])[:, None] * (1e-3 ** expo)[None, :]
         lam_full = np.zeros((args.problems, args.L))
         lam_full[qs] = lams
         t0 = time.perf_counter()
