@@ -19,6 +19,10 @@ Parity status of each function (what pins it in tests/test_oracle.py):
   certify         zero gap at LP optima, positive gap at perturbed points
   lambda_max      b = 0 optimal at lambda_max, not below (simplex)
   grad            central finite differences of refits at generic points
+                  (training y and X rows), of the loss itself (validation
+                  y and X rows); exact scaling by the upstream factor
+Each of 30 planted mistakes in the C source fails at least one of these
+pins (tests/test_oracle_mutants.py).
 """
 from __future__ import annotations
 
