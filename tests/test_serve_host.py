@@ -30,3 +30,143 @@ def test_offsets_ending_at_the_last_new_slot_were_rejected():
     # rule whenever the last slot of the pool is not among the new ones
     S, cap, ss = 8, 300, np.array([0, 2])
     assert not _library_accepts(np.append(ss * cap, (ss[-1] + 1) * cap), S * cap)
+
+
+# ------------------------------------------------------------------ the
+# request loop on CPU tensors, with the four library calls the server makes
+# replaced by a fake that checks each call against the library's rules
+
+
+class FakeLibrary:
+    """Stands in for ladlasso.workspace / lambda_max / lambda_path / fit.
+    lambda_max follows its definition (max_j |X_j^T sign(y)| over the rows
+    a problem uses) so each result can be traced to its own request's data;
+    `fit` moves b by +1 on the used columns per call, so the warm start a
+    slot carries from step to step is visible in the results."""
+
+    def __init__(self, fail_at_step=None):
+        self.calls = 0
+        self.fail_at_step = fail_at_step
+        self.max_used = 0
+
+    def workspace(self, pr, L=1):
+        import torch
+        return torch.empty(16, dtype=torch.uint8)
+
+    def lambda_max(self, pr, ws=None, stream=None):
+        import torch
+        off = pr.offsets.numpy()
+        nr = pr.n_rows.numpy()
+        p = pr.p.numpy()
+        X, y = pr.X.numpy(), pr.y.numpy()
+        B = len(off) - 1
+        out = np.full(B, np.nan, np.float32)
+        # the library's offset rule; a set that breaks it is bad input
+        if _library_accepts(off, y.shape[0]) and np.all(nr <= np.diff(off)):
+            for q in range(B):
+                rows = slice(off[q], off[q] + nr[q])
+                out[q] = np.abs(X[rows, :p[q]].T @ np.sign(y[rows])).max()
+        return torch.from_numpy(out)
+
+    def lambda_path(self, lmax, L, ratio=1e-3, stream=None):
+        import torch
+        t = np.arange(L) / max(1, L - 1)
+        return torch.from_numpy((lmax.numpy()[:, None] * ratio ** t).astype(np.float32))
+
+    def fit(self, pr, lambdas, *, b_init=None, opts=None, ws=None, out=None, **kw):
+        from paper_2510_15649_gb300 import ladlasso as ll
+        self.calls += 1
+        if self.calls == self.fail_at_step:
+            raise ll.LadLassoError("injected failure")
+        lam = lambdas.numpy()[:, 0]
+        nr, p = pr.n_rows.numpy(), pr.p.numpy()
+        active = np.nonzero(np.isfinite(lam))[0]
+        assert np.all(nr[active] > 0), "a slot with a lambda holds no rows"
+        self.max_used = max(self.max_used, int((nr[active] * p[active]).sum()))
+        b0 = b_init.numpy()[:, 0].copy()
+        b, obj, st = out["b"].numpy(), out["obj"].numpy(), out["status"].numpy()
+        for q in range(len(lam)):
+            if q in active:
+                b[q, 0] = 0.0
+                b[q, 0, :p[q]] = b0[q, :p[q]] + 1.0
+                obj[q, 0], st[q, 0] = lam[q], 0
+            else:
+                b[q, 0], obj[q, 0], st[q, 0] = 0.0, 0.0, 2
+        return out
+
+
+@pytest.fixture
+def fake(monkeypatch):
+    from paper_2510_15649_gb300 import ladlasso as ll
+
+    def install(**kw):
+        f = FakeLibrary(**kw)
+        for name in ("workspace", "lambda_max", "lambda_path", "fit"):
+            monkeypatch.setattr(ll, name, getattr(f, name))
+        return f
+    return install
+
+
+def _trace(n=24, seed=3):
+    from paper_2510_15649_gb300 import synth
+    return synth.serve_trace(rate=4000.0, seconds=1.0, seed=seed, n_hi=300, p_hi=8,
+                             max_requests=n)
+
+
+def test_every_request_is_fitted_on_its_own_data_and_warm_started(fake):
+    from paper_2510_15649_gb300.serve import Server
+    f = fake()
+    trace = _trace()
+    L = 3
+    srv = Server(slots=4, cap=300, P=8, L=L, device="cpu")
+    results, st = srv.run(trace, time_scale=1.0)
+    assert st.completed == len(trace) == len(results) and st.bad_fits == 0
+    assert st.fits == len(trace) * L and st.max_active <= 4
+    assert sorted(r.rid for r in results) == list(range(len(trace)))
+    for r in results:
+        X, y = trace[r.rid]["X"], trace[r.rid]["y"]
+        # lambda_max of this request's own rows and columns, then its path
+        lmax = np.abs(X.T @ np.sign(y)).max()
+        np.testing.assert_allclose(r.lambdas[0], lmax, rtol=1e-5)
+        np.testing.assert_allclose(r.lambdas, lmax * 1e-3 ** (np.arange(L) / (L - 1)), rtol=1e-5)
+        # b starts from zero (slots are reused) and is carried step to step
+        assert r.b.shape == (L, X.shape[1])
+        for l in range(L):
+            assert np.all(r.b[l] == l + 1.0)
+        assert np.array_equal(r.obj, r.lambdas) and np.all(r.status == 0)
+        assert r.t_done >= r.t_arrival
+    assert f.calls == st.steps
+
+
+def test_memory_budget_bounds_the_active_work(fake):
+    from paper_2510_15649_gb300.serve import Server
+    f = fake()
+    trace = _trace(n=16, seed=5)
+    budget = int(1.5 * max(r["X"].size for r in trace))
+    srv = Server(slots=8, cap=300, P=8, L=2, budget_floats=budget, device="cpu")
+    results, st = srv.run(trace, time_scale=0.0)  # every request arrives at once
+    assert st.completed == len(trace) and st.bad_fits == 0
+    assert f.max_used <= budget and st.queued_max >= 2
+    assert srv.used == 0 and len(srv.free) == 8  # every slot and byte returned
+
+
+def test_injected_library_failure_reaches_the_caller(fake):
+    from paper_2510_15649_gb300 import ladlasso as ll
+    from paper_2510_15649_gb300.serve import Server
+    fake(fail_at_step=3)
+    srv = Server(slots=4, cap=300, P=8, L=4, device="cpu")
+    with pytest.raises(ll.LadLassoError, match="injected failure"):
+        srv.run(_trace(n=8), time_scale=0.0)
+
+
+def test_request_beyond_slot_capacity_is_refused_on_the_host(fake):
+    from paper_2510_15649_gb300.serve import Server
+    fake()
+    rng = np.random.default_rng(1)
+    big = dict(t=0.0, X=rng.standard_normal((301, 4)).astype(np.float32),
+               y=rng.standard_normal(301).astype(np.float32))
+    wide = dict(t=0.0, X=rng.standard_normal((20, 9)).astype(np.float32),
+                y=rng.standard_normal(20).astype(np.float32))
+    for req in (big, wide):
+        with pytest.raises(ValueError):
+            Server(slots=2, cap=300, P=8, L=2, device="cpu").run([req])
