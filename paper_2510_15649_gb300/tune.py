@@ -116,8 +116,15 @@ def autotune(pr: ll.Problems, lambdas: torch.Tensor, *, opts: ll.Opts | None = N
             e1.synchronize()
             best = min(best, e0.elapsed_time(e1) / 1e3)
         times[c] = best
-    best = min(times.values())
-    near = [c for c, t in times.items() if t <= best * (1.0 + tie)]
-    choice = min(near, key=lambda c: (c.group_threads != 32, c.fits_per_block, c.work_order))
+    choice = choose(times, tie)
     _cache[key] = (choice, times)
     return choice, times
+
+
+def choose(times: dict, tie: float = 0.01):
+    """The shape to use given measured seconds per shape: among shapes
+    within `tie` (relative) of the fastest, the one-warp shape with the
+    fewest fits per block, then work order 0."""
+    best = min(times.values())
+    near = [c for c, t in times.items() if t <= best * (1.0 + tie)]
+    return min(near, key=lambda c: (c.group_threads != 32, c.fits_per_block, c.work_order))

@@ -41,3 +41,40 @@ def test_cache_round_trips_through_json(tmp_path):
     choice, t2 = tune._cache[key]
     assert choice == ll.Launch(32, 3, 0) and t2 == times
     tune._cache.clear()
+
+
+def test_choice_prefers_fewer_fits_within_the_tie():
+    W = lambda f, o=0: ll.Launch(32, f, o)  # noqa: E731
+    blk = ll.Launch(512, 0, 0)
+    # the fastest wins when nothing else is within 1 %
+    assert tune.choose({W(6): 1.00, W(3): 1.05, blk: 2.0}) == W(6)
+    # within the tie: the fewest fits per block, then work order 0
+    assert tune.choose({W(6): 1.000, W(3): 1.005, W(2): 1.2}) == W(3)
+    assert tune.choose({W(3, 1): 1.000, W(3, 0): 1.009}) == W(3, 0)
+    # the one-warp shape before the block shape at equal time
+    assert tune.choose({blk: 1.0, W(6): 1.0}) == W(6)
+    assert tune.choose({blk: 1.0, W(6): 1.5}) == blk
+    # a wider tie admits slower shapes
+    assert tune.choose({W(6): 1.0, W(2): 1.04}, tie=0.05) == W(2)
+
+
+def test_sample_subset_keeps_every_kth_problem():
+    import numpy as np
+    import torch
+    from paper_2510_15649_gb300 import synth
+    b = synth.batched_like(10, 5, 30, 2, 6, R=100, P=6, seed=2)
+    pr = ll.Problems.from_numpy(b, device="cpu")
+    lam = torch.arange(10 * 3, dtype=torch.float32).reshape(10, 3)
+    sub, sl = tune._subset(pr, lam, 3)
+    qs = [0, 3, 6, 9]
+    off = b["offsets"]
+    so = sub.offsets.numpy()
+    assert sub.B == 4 and len(so) == 5
+    for k, q in enumerate(qs):
+        rows = b["row_idx"][off[q]:off[q + 1]]
+        assert np.array_equal(sub.row_idx.numpy()[so[k]:so[k + 1]], rows)
+        assert np.array_equal(sub.y.numpy()[so[k]:so[k + 1]], b["y"][off[q]:off[q + 1]])
+        assert sub.p.numpy()[k] == b["p"][q]
+        assert np.array_equal(sl[k].numpy(), lam[q].numpy())
+    assert so[-1] == sub.y.numel()  # the library's rule: the set ends at its row count
+    assert sub.X is pr.X and sub.n_max == pr.n_max
