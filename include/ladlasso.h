@@ -95,7 +95,8 @@ typedef struct ladlasso_opts {
 void ladlasso_default_opts(ladlasso_opts* o);
 
 /* Problem-set dimensions and optional side arrays.
- * B        problems (>= 0)                    P_cols  columns used for b (1..256)
+ * B        problems (>= 0)                    P_cols  columns used for b (1..256;
+ *                                              the batched fit holds about 220 at most)
  * L        path length (>= 1)                 ldX     row stride of X (>= P_cols)
  * rows_X   rows of X (row_idx range check)    total_rows  offsets[B] (slots)
  * n_max    host-known bound on n_q; problems with more rows get BAD_INPUT
@@ -127,6 +128,11 @@ void ladlasso_default_opts(ladlasso_opts* o);
  *            0 = automatic (one warp per fit up to 8192 rows, else one
  *            512-thread block per fit), 32 = one warp per fit, 512 = one
  *            block per fit; any other value is LADLASSO_ERR_INVALID.  The
+ *            automatic choice looks at n_max only: from P_cols = 159 one
+ *            warp's share of shared memory holds fewer than 8192 rows, and
+ *            n_max between that limit and 8192 returns LADLASSO_ERR_NOMEM
+ *            unless 512 is asked for (ladlasso_launch_shape gives both
+ *            limits; the autotuner offers only shapes that hold n_max).  The
  *            two shapes sum in different orders: results agree within the
  *            float32 tolerance, not bit for bit
  * fits_per_block  one-warp shape: at most this many fits per thread block
@@ -183,7 +189,8 @@ int ladlasso_lambda_path(const float* lmax, int32_t B, int32_t L, float ratio,
  * shared memory, the columns streamed from the gathered design in the
  * workspace.  Warps (blocks) take problems from a device work queue, longest
  * first.  LADLASSO_ERR_NOMEM when n_max exceeds what one block's shared
- * memory holds (about 34000 rows at P_cols = 128).
+ * memory holds (23,385 rows at P_cols = 128; no row count beyond about 220
+ * columns); ladlasso_launch_shape reports the exact limit.
  *   lambdas [B*L], b_out [B*L*P_cols], obj_out [B*L] device.
  * obj_out holds F at the returned b. */
 int ladlasso_fit_batched(const float* X, const float* y, const int32_t* row_idx,
