@@ -128,6 +128,71 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _need(t, name: str, dtype, dev, numel: int | None = None):
+    """Raise unless tensor `t` (None allowed) is a contiguous `dtype` tensor
+    on device `dev` with `numel` elements: the library reads raw pointers,
+    so a host tensor, another dtype or a strided view would be misread."""
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor):
+        raise LadLassoError(f"{name} must be a torch tensor")
+    if t.device != dev:
+        raise LadLassoError(f"{name} is on {t.device}; the problem set is on {dev}")
+    if t.dtype != dtype:
+        raise LadLassoError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise LadLassoError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise LadLassoError(f"{name} has {t.numel()} elements, expected {numel}")
+
+
+def _check_problems(pr: "Problems") -> None:
+    """A problem set the library can read: CUDA tensors of the documented
+    types (include/ladlasso.h), X row-major with at least P columns."""
+    X = pr.X
+    if not isinstance(X, torch.Tensor) or X.device.type != "cuda":
+        raise LadLassoError("the problem set must be in CUDA device memory "
+                            f"(X is on {getattr(X, 'device', type(X))})")
+    _check_layout(pr)
+
+
+def _check_layout(pr: "Problems") -> None:
+    """Types, shapes and strides of a problem set, all on X's device."""
+    X = pr.X
+    dev = X.device
+    if X.dtype != torch.float32 or X.dim() != 2:
+        raise LadLassoError(f"X must be a 2-D float32 tensor, got {X.dtype} with {X.dim()} dims")
+    if X.shape[1] < pr.P or (X.shape[0] > 0 and X.stride(1) != 1) or \
+            (X.shape[0] > 1 and X.stride(0) < X.shape[1]):
+        raise LadLassoError(f"X must be row-major with at least P = {pr.P} columns")
+    _need(pr.y, "y", torch.float32, dev)
+    if pr.y.dim() != 1:
+        raise LadLassoError("y must be 1-D")
+    _need(pr.offsets, "offsets", torch.int64, dev)
+    if pr.offsets.numel() < 1:
+        raise LadLassoError("offsets needs B + 1 >= 1 entries")
+    _need(pr.row_idx, "row_idx", torch.int32, dev, int(pr.y.numel()))
+    _need(pr.p, "p", torch.int32, dev, pr.B)
+    _need(pr.n_rows, "n_rows", torch.int32, dev, pr.B)
+
+
+_OUT_KINDS = {"b": (torch.float32, 3), "obj": (torch.float32, 1), "status": (torch.int32, 1),
+              "basis": (torch.int32, 3), "counters": (torch.int32, 0)}
+
+
+def _check_out(out: dict, B: int, L: int, P: int, dev, required=("b", "obj", "status")):
+    """Result buffers handed to the library: b [B,L,P] and obj [B,L]
+    float32, status [B,L], basis [B,L,P] and counters [B,L,8] int32."""
+    for k in required:
+        if k not in out:
+            raise LadLassoError(f"out needs {k!r}")
+    for k, t in out.items():
+        if k in _OUT_KINDS:
+            dtype, kind = _OUT_KINDS[k]
+            per = P if kind == 3 else (8 if kind == 0 else 1)
+            _need(t, f"out[{k!r}]", dtype, dev, B * L * per)
+
+
 def _stream(stream):
     s = torch.cuda.current_stream() if stream is None else stream
     return C.c_void_p(s.cuda_stream)
@@ -166,6 +231,7 @@ class Problems:
 
     def dims(self, L: int, workspace: torch.Tensor, opts: Opts | None = None, b_init=None,
              status=None, basis=None, counters=None) -> Dims:
+        _check_problems(self)
         d = Dims()
         d.B, d.P_cols, d.L, d.n_max = self.B, self.P, L, self.n_max
         d.ldX = int(self.X.stride(0))
@@ -208,6 +274,10 @@ def lambda_max(pr: Problems, ws: torch.Tensor | None = None, stream=None) -> tor
 
 def lambda_path(lmax: torch.Tensor, L: int, ratio: float = 1e-3, stream=None) -> torch.Tensor:
     B = int(lmax.numel())
+    if lmax.device.type != "cuda":
+        raise LadLassoError(f"lmax must be in CUDA device memory (it is on {lmax.device})")
+    lmax = lmax.contiguous()
+    _need(lmax, "lmax", torch.float32, lmax.device)
     out = torch.empty((B, L), dtype=torch.float32, device=lmax.device)
     _check(lib().ladlasso_lambda_path(_ptr(lmax), B, L, float(ratio), _ptr(out), _stream(stream)))
     return out
@@ -242,11 +312,15 @@ def fit(pr: Problems, lambdas: torch.Tensor, *, b_init=None, opts: Opts | None =
     """Fit every problem along its lambda path.  lambdas: [B, L] float32 (device).
     `launch` overrides the launch shape (see tune.autotune).
     Returns dict(b [B,L,P], obj [B,L], status [B,L], basis?, counters?)."""
+    _check_problems(pr)
     B, P = pr.B, pr.P
-    lam = lambdas.reshape(B, -1)
+    lam = lambdas.reshape(B, -1).contiguous()
     L = int(lam.shape[1])
     dev = pr.X.device
+    _need(lam, "lambdas", torch.float32, dev)
+    _need(b_init, "b_init", torch.float32, dev, B * P)
     ws = workspace(pr, L) if ws is None else ws
+    _need(ws, "workspace", torch.uint8, dev)
     if out is None:
         out = dict(b=torch.empty((B, L, P), dtype=torch.float32, device=dev),
                    obj=torch.empty((B, L), dtype=torch.float32, device=dev),
@@ -255,6 +329,7 @@ def fit(pr: Problems, lambdas: torch.Tensor, *, b_init=None, opts: Opts | None =
             out["basis"] = torch.empty((B, L, P), dtype=torch.int32, device=dev)
         if counters:
             out["counters"] = torch.empty((B, L, 8), dtype=torch.int32, device=dev)
+    _check_out(out, B, L, P, dev)
     d = pr.dims(L, ws, opts, b_init=b_init, status=out["status"], basis=out.get("basis"),
                 counters=out.get("counters"))
     if launch is not None:
@@ -262,7 +337,7 @@ def fit(pr: Problems, lambdas: torch.Tensor, *, b_init=None, opts: Opts | None =
         d.work_order = launch.work_order
     fn = lib().ladlasso_fit_batched_thread if per_thread else lib().ladlasso_fit_batched
     with _nvtx("ladlasso_fit_batched_thread" if per_thread else "ladlasso_fit_batched"):
-        _check(fn(_ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), _ptr(lam.contiguous()),
+        _check(fn(_ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), _ptr(lam),
                   _ptr(out["b"]), _ptr(out["obj"]), C.byref(d), _stream(stream)))
     return out
 
@@ -270,7 +345,12 @@ def fit(pr: Problems, lambdas: torch.Tensor, *, b_init=None, opts: Opts | None =
 def path_loss(val: Problems, b: torch.Tensor, stream=None) -> torch.Tensor:
     """sum_v |y_v - x_v . b[q, l]| over the rows of problem q of `val`, for
     every path position l of b [B, L, P] (device).  Returns [B, L]."""
+    _check_problems(val)
     B = val.B
+    b = b.contiguous()
+    if b.dim() != 3 or b.shape[0] != B or b.shape[2] != val.P:
+        raise LadLassoError(f"b must be [B={B}, L, P={val.P}], got {tuple(b.shape)}")
+    _need(b, "b", torch.float32, val.X.device)
     L = int(b.shape[1])
     out = torch.empty((B, L), dtype=torch.float32, device=val.X.device)
     d = val.dims(L, out)
@@ -286,9 +366,12 @@ def fit_noalloc(pr: Problems, lambdas: torch.Tensor, *, opts: Opts | None = None
     scratch array instead of a workspace.  `out` holds preallocated
     b [B,L,P], obj [B,L], status [B,L] device tensors (nothing is allocated
     here either)."""
+    _check_problems(pr)
     B = pr.B
-    lam = lambdas.reshape(B, -1)
+    lam = lambdas.reshape(B, -1).contiguous()
     L = int(lam.shape[1])
+    _need(lam, "lambdas", torch.float32, pr.X.device)
+    _check_out(out, B, L, pr.P, pr.X.device)
     d = pr.dims(L, out["obj"], opts, status=out["status"])
     d.workspace = None
     d.workspace_bytes = 0
@@ -303,10 +386,20 @@ def fit_backward(pr: Problems, fwd: dict, pos: int, val: Problems, grad_up: torc
     """Gradient of sum_v |y_v - x_v b| per problem at path position `pos`
     of a forward result that carries `basis`.  Returns dict(lam [B], y, X,
     yv, Xv, status [B], loss [B])."""
+    _check_problems(pr)
+    _check_problems(val)
     B, P = pr.B, pr.P
+    if "basis" not in fwd:
+        raise LadLassoError("the forward result needs its basis: fit(..., basis=True)")
     L = int(fwd["b"].shape[1])
     dev = pr.X.device
+    if val.X.device != dev or val.X.shape[1] < P:
+        raise LadLassoError(f"validation rows must be on {dev} with at least P = {P} columns")
+    if not 0 <= pos < L:
+        raise LadLassoError(f"path position {pos} outside 0..{L - 1}")
+    _check_out(dict(b=fwd["b"], basis=fwd["basis"]), B, L, P, dev, required=("b", "basis"))
     ws = workspace(pr, L) if ws is None else ws
+    _need(ws, "workspace", torch.uint8, dev)
     g = dict(lam=torch.empty(B, dtype=torch.float32, device=dev),
              y=torch.empty(pr.y.numel(), dtype=torch.float32, device=dev),
              X=torch.empty((pr.y.numel(), P), dtype=torch.float32, device=dev),
@@ -316,6 +409,7 @@ def fit_backward(pr: Problems, fwd: dict, pos: int, val: Problems, grad_up: torc
              loss=torch.empty(B, dtype=torch.float32, device=dev))
     d = pr.dims(L, ws, opts)
     up = grad_up.contiguous().float()
+    _need(up, "grad_up", torch.float32, dev, B)
     with _nvtx("ladlasso_fit_backward"):
         _check(lib().ladlasso_fit_backward(
             _ptr(pr.X), _ptr(pr.y), _ptr(pr.row_idx), _ptr(pr.offsets), C.byref(d), int(pos),
