@@ -17,6 +17,60 @@ def shard_range(B: int, rank: int, world: int) -> tuple:
     return lo, lo + base + (1 if rank < extra else 0)
 
 
+def cost_shard_range(cost, rank: int, world: int) -> tuple:
+    """Contiguous share [lo, hi) of the problems for `rank` of `world`,
+    balanced by per-problem cost (e.g. n * p * L, the work a fit does
+    along its path): rank r's share ends at the prefix whose running cost
+    is nearest to (r + 1) / world of the total, so every boundary is within
+    half a problem's cost of its target and every rank's cost within one
+    problem's cost of total / world.  Contiguous shares keep every rank's
+    problems one slice of the offsets."""
+    import numpy as np
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad shard arguments")
+    c = np.asarray(cost, np.float64)
+    if c.ndim != 1 or np.any(c < 0) or not np.all(np.isfinite(c)):
+        raise ValueError("costs must be a finite non-negative vector")
+    B = len(c)
+    if B == 0:
+        return 0, 0
+    cum = np.cumsum(c)
+    total = cum[-1]
+    if total <= 0:
+        return shard_range(B, rank, world)
+
+    def end(r):  # the prefix length whose running cost is nearest the target
+        if r == world - 1:
+            return B
+        t = total * (r + 1) / world
+        k = int(np.searchsorted(cum, t, side="left"))  # cum[k] >= t > cum[k-1]
+        below = cum[k - 1] if k > 0 else 0.0
+        return k + 1 if cum[k] - t < t - below else k
+
+    lo = 0 if rank == 0 else min(end(rank - 1), B)
+    hi = max(lo, min(end(rank), B))
+    return lo, hi
+
+
+def shard_batch(batch: dict, lo: int, hi: int) -> dict:
+    """Problems lo..hi-1 of a batch (the layout of `synth`) as a batch of
+    their own: the same shared X, their slots of y / row_idx, offsets
+    rebased to start at 0."""
+    import numpy as np
+    off = np.asarray(batch["offsets"], np.int64)
+    a, b = int(off[lo]), int(off[hi])
+    ri = batch.get("row_idx")
+    out = dict(batch)
+    out.update(y=batch["y"][a:b], offsets=off[lo:hi + 1] - a,
+               p=np.asarray(batch["p"])[lo:hi])
+    if ri is None:
+        out["X"] = batch["X"][a:b]  # slots are rows of X
+        out["row_idx"] = None
+    else:
+        out["row_idx"] = ri[a:b]
+    return out
+
+
 def max_over_ranks(value: float, dist=None, device=None) -> float:
     """Largest `value` over the ranks of the default process group (the
     value itself without one)."""
