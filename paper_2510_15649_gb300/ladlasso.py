@@ -263,7 +263,9 @@ def workspace(pr: Problems, L: int = 1) -> torch.Tensor:
 
 
 def lambda_max(pr: Problems, ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    _check_problems(pr)
     ws = workspace(pr) if ws is None else ws
+    _need(ws, "workspace", torch.uint8, pr.X.device)
     out = torch.empty(pr.B, dtype=torch.float32, device=pr.X.device)
     d = pr.dims(1, ws)
     with _nvtx("ladlasso_lambda_max"):
