@@ -7,8 +7,8 @@ longest first or longest and shortest alternately.  More fits per block
 hide more latency but also keep more gathered designs live in L2 at once,
 so the best choice depends on the problem mix.  `autotune` times every
 candidate on an evenly strided sample of the problem set (same size mix)
-with CUDA events and returns the fastest; choices are cached per device and
-problem-set signature.  Per-fit results do not depend on fits_per_block;
+with CUDA events and returns the fastest; choices are cached per device,
+problem-set signature and options (`cache_key`).  Per-fit results do not depend on fits_per_block;
 the two shapes agree within the float32 tolerance.
 """
 from __future__ import annotations
@@ -47,6 +47,16 @@ def load_cache(path: str) -> int:
             times[ll.Launch(int(gs), int(fs), int(os_))] = float(t)
         _cache[tuple(r["key"])] = (ll.Launch(g, fb, o), times)
     return len(rows)
+
+
+def cache_key(pr: ll.Problems, L: int, opts: ll.Opts | None = None, device_name: str = "") -> tuple:
+    """Signature under which a choice is cached (flat, so it survives the
+    JSON file): device, problem-set shape (P, n_max, B, path length, total
+    rows, row-index layout) and every method option, which all change the
+    work per fit."""
+    o = opts if opts is not None else ll.default_opts()
+    return (device_name, pr.P, pr.n_max, pr.B, L, pr.row_idx is None, int(pr.y.numel()),
+            *(getattr(o, f) for f, _ in o._fields_))
 
 
 def candidates(pr: ll.Problems) -> list:
@@ -93,7 +103,7 @@ def autotune(pr: ll.Problems, lambdas: torch.Tensor, *, opts: ll.Opts | None = N
     Returns (Launch, {shape: seconds})."""
     L = int(lambdas.reshape(pr.B, -1).shape[1])
     dev = pr.X.device
-    key = (torch.cuda.get_device_name(dev), pr.P, pr.n_max, pr.B, L, pr.row_idx is None)
+    key = cache_key(pr, L, opts, torch.cuda.get_device_name(dev))
     if use_cache and key in _cache:
         return _cache[key]
     cands = candidates(pr)

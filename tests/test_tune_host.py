@@ -29,18 +29,41 @@ def test_no_candidate_beyond_every_shape():
     assert tune.candidates(Pr(128, 10 ** 6)) == []
 
 
-def test_cache_round_trips_through_json(tmp_path):
+def _cpu_problems(B=6, seed=2):
+    from paper_2510_15649_gb300 import synth
+    return ll.Problems.from_numpy(synth.batched_like(B, 5, 30, 2, 6, R=60, P=6, seed=seed),
+                                  device="cpu")
+
+
+def test_cache_round_trips_through_json():
+    import os
     tune._cache.clear()
-    key = ("GB300", 32, 2000, 4096, 16, False)
+    key = tune.cache_key(_cpu_problems(), 16, None, "GB300")
     times = {ll.Launch(32, 3, 0): 1.046, ll.Launch(32, 5, 1): 1.107, ll.Launch(512, 0, 0): 2.0}
     tune._cache[key] = (ll.Launch(32, 3, 0), times)
-    path = str(tmp_path / "tune.json")
-    tune.save_cache(path)
-    tune._cache.clear()
-    assert tune.load_cache(path) == 1
+    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_build")
+    os.makedirs(d, exist_ok=True)
+    path = os.path.join(d, f"tune_cache_test_{os.getpid()}.json")
+    try:
+        tune.save_cache(path)
+        tune._cache.clear()
+        assert tune.load_cache(path) == 1
+    finally:
+        os.remove(path)
     choice, t2 = tune._cache[key]
     assert choice == ll.Launch(32, 3, 0) and t2 == times
     tune._cache.clear()
+
+
+def test_cache_key_tells_problem_sets_and_options_apart():
+    a, b = _cpu_problems(seed=2), _cpu_problems(seed=3)
+    assert int(a.y.numel()) != int(b.y.numel())
+    assert tune.cache_key(a, 4) == tune.cache_key(a, 4, ll.default_opts())
+    assert tune.cache_key(a, 4) != tune.cache_key(b, 4)
+    assert tune.cache_key(a, 4) != tune.cache_key(a, 5)
+    assert tune.cache_key(a, 4) != tune.cache_key(a, 4, ll.default_opts(chop_sections=4))
+    assert tune.cache_key(a, 4, None, "x") != tune.cache_key(a, 4, None, "y")
+    hash(tune.cache_key(a, 4))
 
 
 def test_choice_prefers_fewer_fits_within_the_tie():
