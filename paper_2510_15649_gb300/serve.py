@@ -159,6 +159,9 @@ class Server:
                 n, p = trace[i]["X"].shape
                 if n > self.cap or p > self.P:
                     raise ValueError(f"request {i} ({n}x{p}) exceeds the slot capacity")
+                if n * p > self.budget:
+                    raise ValueError(f"request {i} ({n}x{p}) exceeds the memory budget "
+                                     f"of {self.budget} floats on its own")
                 if self.used + extra + n * p > self.budget:
                     break  # device-memory admission: wait for requests to retire
                 queue.pop(0)

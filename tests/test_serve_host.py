@@ -170,3 +170,17 @@ def test_request_beyond_slot_capacity_is_refused_on_the_host(fake):
     for req in (big, wide):
         with pytest.raises(ValueError):
             Server(slots=2, cap=300, P=8, L=2, device="cpu").run([req])
+
+
+def test_request_beyond_the_memory_budget_is_refused_not_queued_forever(fake):
+    from paper_2510_15649_gb300.serve import Server
+    fake()
+    rng = np.random.default_rng(2)
+    req = dict(t=0.0, X=rng.standard_normal((100, 4)).astype(np.float32),
+               y=rng.standard_normal(100).astype(np.float32))
+    srv = Server(slots=2, cap=300, P=8, L=2, budget_floats=399, device="cpu")
+    with pytest.raises(ValueError, match="memory budget"):
+        srv.run([req])
+    # exactly at the budget it is served
+    results, st = Server(slots=2, cap=300, P=8, L=2, budget_floats=400, device="cpu").run([req])
+    assert st.completed == 1
