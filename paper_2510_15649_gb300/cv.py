@@ -37,7 +37,10 @@ class CVResult:
 
 def kfold_splits(n: int, K: int, seed: int = 0) -> list:
     """K disjoint held-out folds of a seeded permutation of the n rows;
-    returns [(train_rows, heldout_rows)] with sorted row indices."""
+    returns [(train_rows, heldout_rows)] with sorted row indices.
+    2 <= K <= n, so that every fold holds rows out and keeps rows to fit."""
+    if not 2 <= K <= n:
+        raise ValueError(f"K-fold needs 2 <= K <= n (K = {K}, n = {n})")
     perm = np.random.default_rng(seed).permutation(n)
     folds = np.array_split(perm, K)
     return [(np.sort(np.concatenate(folds[:k] + folds[k + 1:])), np.sort(folds[k]))
@@ -46,7 +49,9 @@ def kfold_splits(n: int, K: int, seed: int = 0) -> list:
 
 def subset_splits(n: int, m: int, S: int, seed: int = 0) -> list:
     """S random leave-m-out splits (m held-out rows each, drawn without
-    replacement within a split)."""
+    replacement within a split); 1 <= m < n."""
+    if not 1 <= m < n or S < 1:
+        raise ValueError(f"leave-m-out needs 1 <= m < n and S >= 1 (m = {m}, n = {n}, S = {S})")
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(S):

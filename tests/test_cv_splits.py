@@ -18,6 +18,17 @@ def test_kfold_partitions_the_rows():
         assert abs(len(ho) - 103 / 5) < 1
 
 
+def test_split_arguments_are_checked():
+    import pytest
+    for n, K in [(10, 1), (10, 11), (0, 2)]:
+        with pytest.raises(ValueError):
+            kfold_splits(n, K)
+    for n, m, S in [(10, 0, 3), (10, 10, 3), (10, 3, 0)]:
+        with pytest.raises(ValueError):
+            subset_splits(n, m, S)
+    assert len(kfold_splits(10, 10)) == 10  # leave-one-out
+
+
 def test_subset_splits_hold_out_m_rows():
     sp = subset_splits(50, 7, 9, seed=1)
     assert len(sp) == 9
