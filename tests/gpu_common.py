@@ -73,3 +73,27 @@ def compare(batch, lam, b_gpu, obj_gpu, status_gpu, problems=None, opts=None):
             if np.any(b_gpu[q, l, p:] != 0):
                 bad.append((q, l, "padding"))
     return dict(bad=bad, worst_obj=worst_obj, worst_coef=worst_coef, checked=checked)
+
+
+def _compare_chunk(args):
+    batch, lam, b_gpu, obj_gpu, status_gpu, problems, opts = args
+    return compare(batch, lam, b_gpu, obj_gpu, status_gpu, problems=problems, opts=opts)
+
+
+def compare_parallel(batch, lam, b_gpu, obj_gpu, status_gpu, problems, opts=None, workers=8):
+    """compare() over `problems` split across worker processes (started by
+    spawn, so safe after CUDA has been initialised in this process); merges
+    the counts and worst errors."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    problems = list(problems)
+    w = max(1, min(workers, os.cpu_count() or 1, len(problems)))
+    chunks = [problems[k::w] for k in range(w)]
+    jobs = [(batch, lam, b_gpu, obj_gpu, status_gpu, c, opts) for c in chunks if c]
+    with ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        parts = list(ex.map(_compare_chunk, jobs))
+    return dict(bad=[x for r in parts for x in r["bad"]],
+                worst_obj=max(r["worst_obj"] for r in parts),
+                worst_coef=max(r["worst_coef"] for r in parts),
+                checked=sum(r["checked"] for r in parts))

@@ -1,0 +1,56 @@
+"""The headline workload at full size: 4096 problems (row subsets of a
+shared 2000 x 32 design, n ~ U[50, 2000], p ~ U[4, 32]) along a 16-point
+path in one launch, in the launch shapes the benchmark times, checked
+against the FP64 oracle on problems sampled across the size range (the
+oracle cannot afford all 65,536 fits); the launch shapes agree bit for bit."""
+import numpy as np
+import pytest
+
+from gpu_common import compare_parallel
+from paper_2510_15649_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+L = 16
+
+
+@pytest.fixture(scope="module")
+def ll():
+    import torch  # noqa: F401
+    from paper_2510_15649_gb300 import build
+    build.build()
+    from paper_2510_15649_gb300 import ladlasso
+    return ladlasso
+
+
+def sample_problems(batch, k=12):
+    """k problems at evenly spaced ranks of n (smallest and largest included)."""
+    n = np.diff(batch["offsets"])
+    order = np.argsort(n, kind="stable")
+    picks = order[np.linspace(0, len(n) - 1, k).round().astype(int)]
+    return sorted(set(int(q) for q in picks))
+
+
+def test_headline_workload_sampled_parity(ll):
+    import torch
+    batch = synth.batched()
+    pr = ll.Problems.from_numpy(batch)
+    assert pr.B == 4096 and pr.P == 32
+    lam = ll.lambda_path(ll.lambda_max(pr), L, 1e-3)
+    runs = {}
+    for tag, launch in [("auto", None), ("32x3/o0", ll.Launch(32, 3, 0)),
+                        ("32x6/o1", ll.Launch(32, 6, 1))]:
+        out = ll.fit(pr, lam, launch=launch)
+        torch.cuda.synchronize()
+        runs[tag] = {k: v.cpu().numpy() for k, v in out.items()}
+    ref = runs["auto"]
+    # one launch shape's per-fit arithmetic does not depend on fits per
+    # block or on the order problems are taken in
+    for tag in ("32x3/o0", "32x6/o1"):
+        for k in ("b", "obj", "status"):
+            assert np.array_equal(runs[tag][k], ref[k]), (tag, k)
+    assert not np.any(ref["status"] & 2)  # no fit reports bad input
+    qs = sample_problems(batch)
+    res = compare_parallel(batch, lam.cpu().numpy(), ref["b"], ref["obj"], ref["status"], qs)
+    assert res["checked"] == len(qs) * L
+    assert not res["bad"], res["bad"][:10]
