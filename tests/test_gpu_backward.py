@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from gpu_common import LAM_REL, MARGIN
 from paper_2510_15649_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -39,10 +40,55 @@ def test_backward_matches_oracle_active_set_gradient(ll):
     g = ll.fit_backward(ptr, fwd, 0, pva, up)
     torch.cuda.synchronize()
     g = {k: v.cpu().numpy() for k, v in g.items()}
-    bg = fwd["b"].cpu().numpy()[:, 0]
-    upn = up.cpu().numpy()
+    checked = _check_against_oracle(g, fwd["b"].cpu().numpy()[:, 0], lam, up.cpu().numpy(),
+                                    tr, va, range(B))
+    assert checked >= B // 2
+
+
+def test_backward_full_size_sampled(ll):
+    # the differentiation workload as the benchmark runs it: 512 problems of
+    # 400 training and 100 validation rows, 16 columns, lambda = 0.1 lambda_max
+    # of the training rows (computed on the GPU); 32 problems compared
+    import torch
+    d = synth.diff()
+    tr, va = d["train"], d["val"]
+    ptr, pva = ll.Problems.from_numpy(tr), ll.Problems.from_numpy(va)
+    B = ptr.B
+    assert B == 512 and ptr.P == 16
+    lam_t = (0.1 * ll.lambda_max(ptr)).reshape(B, 1).contiguous()
+    fwd = ll.fit(ptr, lam_t, basis=True)
+    up = torch.ones(B, device="cuda")
+    g = ll.fit_backward(ptr, fwd, 0, pva, up)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in g.items()}
+    qs = range(0, B, 16)
+    checked = _check_against_oracle(g, fwd["b"].cpu().numpy()[:, 0], lam_t.cpu().numpy()[:, 0],
+                                    up.cpu().numpy(), tr, va, qs, separated_only=True)
+    assert checked >= len(qs) // 2
+
+
+def _well_separated(X, y, ref, lam):
+    """The parity bar's uniqueness test (tests/gpu_common.py): a strict
+    vertex with complementarity margin >= MARGIN whose support is the same
+    at lambda * (1 -+ LAM_REL), so float32 cannot land on another vertex."""
+    _, info = oracle.certify(X, y, ref["b"][0], lam)
+    if not info["unique"] or min(1.0 - info["u_e_max"], 1.0 - info["c_off_max"]) < MARGIN:
+        return False
+    sup = ref["b"][0] != 0
+    return all(np.array_equal(oracle.fit_path(X, y, [lam * (1.0 + sg * LAM_REL)],
+                                              b_init=ref["b"][0])["b"][0] != 0, sup)
+               for sg in (-1.0, 1.0))
+
+
+def _check_against_oracle(g, bg, lam, upn, tr, va, qs, separated_only=False):
+    """Per sampled problem: the validation loss at the GPU's coefficients,
+    and, where both sides end at a strict vertex (well separated from its
+    neighbours at float32 resolution when `separated_only`), every gradient
+    entry within 1e-3 max(1, |g|) of the oracle's active-set gradient and a
+    zero lambda derivative.  Returns how many problems had their gradient
+    checked."""
     checked = 0
-    for q in range(B):
+    for q in qs:
         X, y = oracle.problem(tr, q)
         Xv, yv = oracle.problem(va, q)
         o0, o1 = tr["offsets"][q], tr["offsets"][q + 1]
@@ -53,6 +99,8 @@ def test_backward_matches_oracle_active_set_gradient(ll):
         assert abs(g["loss"][q] - lv) <= 1e-5 * max(1.0, lv)
         if ref["status"][0] != oracle.FIT_OK or g["status"][q] != 0:
             continue  # not a strict vertex: the gradient is not defined there
+        if separated_only and not _well_separated(X, y, ref, float(lam[q])):
+            continue
         og = oracle.grad(X, y, ref["b"][0], ref["basis"][0], Xv, yv, up=float(upn[q]))
         assert og["ok"]
         tol = lambda a: 1e-3 * np.maximum(1.0, np.abs(a))
@@ -62,7 +110,7 @@ def test_backward_matches_oracle_active_set_gradient(ll):
         assert np.all(np.abs(g["Xv"][v0:v1] - og["gXv"]) <= tol(og["gXv"]))
         assert g["lam"][q] == 0.0
         checked += 1
-    assert checked >= B // 2
+    return checked
 
 
 def test_autograd_function_matches_backward_entry_point(ll):
