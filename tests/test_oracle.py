@@ -69,6 +69,27 @@ def test_simplex_matches_scipy_highs():
             assert rel(fs, res.fun) < 1e-9, (n, p, lam, fs, res.fun)
 
 
+def test_dual_lp_value_equals_the_method_optimum():
+    # strong duality for the LP of Section 3.1 with lambda on |b|_1: the
+    # optimum equals max y.u over |u_i| <= 1, |(X^T u)_j| <= lambda (the
+    # bounded dual form), solved here by scipy's HiGHS, independently of
+    # the oracle's simplex, brute force and certificate
+    linprog = pytest.importorskip("scipy.optimize").linprog
+    rng = np.random.default_rng(12)
+    for n, p in [(15, 2), (40, 4), (80, 6)]:
+        X, y = rand_problem(rng, n, p)
+        for lam in [0.1, 2.0, 0.9 * oracle.lambda_max(X, y)]:
+            r = oracle.fit_path(X, y, [lam])
+            A = np.vstack([X.T, -X.T])
+            dual = linprog(-y, A_ub=A, b_ub=lam * np.ones(2 * p), bounds=(-1, 1), method="highs")
+            assert dual.status == 0
+            assert rel(r["f"][0], -dual.fun) < 1e-9, (n, p, lam, r["f"][0], -dual.fun)
+            # and the certificate's dual point is feasible with the same value
+            gap, info = oracle.certify(X, y, r["b"][0], lam)
+            assert abs(gap) <= 1e-8 * max(1.0, r["f"][0])
+            assert rel(info["dual"], -dual.fun) < 1e-8
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_random_tiny_brute_equals_simplex_equals_method(seed):
     rng = np.random.default_rng(100 + seed)

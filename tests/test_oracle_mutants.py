@@ -127,6 +127,7 @@ PINS = [
     ("test_fit_batch_matches_single_fits", ()),
     ("test_active_set_gradient_matches_finite_differences", ()),
     ("test_simplex_matches_scipy_highs", ()),
+    ("test_dual_lp_value_equals_the_method_optimum", ()),
     ("test_medium_method_equals_simplex_and_certificate", ()),
 ]
 
