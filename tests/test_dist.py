@@ -8,7 +8,8 @@ import numpy as np
 import pytest
 
 from paper_2510_15649_gb300 import synth
-from paper_2510_15649_gb300.dist import cost_shard_range, max_over_ranks, shard_batch, shard_range
+from paper_2510_15649_gb300.dist import (cost_shard_range, max_over_ranks, shard_batch, shard_range,
+                                         sum_over_ranks)
 
 
 def test_shards_cover_every_problem_once():
@@ -83,6 +84,7 @@ def _worker(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     lo, hi = shard_range(10, rank, world)
     t = max_over_ranks(1.0 + rank, dist)
+    total = sum_over_ranks(1.0 + rank, dist)
     # cost-balanced shares of one batch: every problem fitted exactly once
     import torch
     b = synth.batched_like(40, 5, 200, 2, 8, R=250, P=8, seed=7)
@@ -93,7 +95,7 @@ def _worker(rank, world, port, out):
     done[clo:chi] = 1
     dist.all_reduce(done)
     mine = float(np.sum(np.diff(part["offsets"]) * part["p"]))
-    out.put((rank, lo, hi, t, done.tolist(), mine, float(cost.sum())))
+    out.put((rank, lo, hi, t, done.tolist(), mine, float(cost.sum()), total))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -117,3 +119,5 @@ def test_two_gloo_ranks_agree_on_max_time():
     assert (res[0][1], res[0][2], res[1][1], res[1][2]) == (0, 5, 5, 10)
     assert res[0][4] == [1] * 40 and res[1][4] == [1] * 40
     assert res[0][5] + res[1][5] == res[0][6]
+    assert [r[7] for r in res] == [3.0, 3.0]
+    assert sum_over_ranks(2.5) == 2.5 and max_over_ranks(2.5) == 2.5  # no process group
