@@ -65,3 +65,18 @@ def test_launch_shape_is_host_only_and_consistent():
     import pytest
     with pytest.raises(ll.LadLassoError):
         ll.launch_shape(Pr(32, 2000), ll.Launch(64, 0))
+
+
+def test_documented_option_defaults_match_the_library():
+    # each ladlasso_opts field's comment in include/ladlasso.h ends with its
+    # default in parentheses; ladlasso_default_opts must fill exactly those
+    from paper_2510_15649_gb300 import ladlasso
+    src = open(os.path.join(ROOT, "include", "ladlasso.h")).read()
+    body = src[src.index("typedef struct ladlasso_opts"):src.index("} ladlasso_opts;")]
+    fields = re.findall(r"(?:float|int32_t)\s+(\w+);(.*?)(?=(?:float|int32_t)\s+\w+;|\Z)", body, re.S)
+    o = ladlasso.default_opts()
+    assert len(fields) == len(o._fields_)
+    for name, comment in fields:
+        doc = re.findall(r"\(([-0-9.e]+)\)", comment)
+        assert doc, name
+        assert abs(float(doc[-1]) - getattr(o, name)) <= 1e-6 * max(1.0, abs(float(doc[-1]))), name
