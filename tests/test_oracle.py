@@ -438,3 +438,22 @@ def test_bad_lambda_status():
     assert list(r["status"][[1, 2]]) == [oracle.FIT_BAD_INPUT] * 2
     assert np.all(r["b"][1:3] == 0)
     assert r["status"][3] in (0, oracle.FIT_NONUNIQUE)
+
+
+def test_exact_finish_makes_the_result_independent_of_chop_settings():
+    # the vertex polish certifies the LP optimum whatever the chop did (or
+    # whether it ran), so the optimum value does not depend on the chop's
+    # hyper-parameters or the descent tolerance; each setting also matches
+    # the dense simplex
+    rng = np.random.default_rng(21)
+    settings = [dict(), dict(chop=0), dict(chop_sections=4), dict(tol_move=1e-3),
+                dict(chop=0, tol_move=1e-3), dict(chop_max_probes=2, probe_max_sweeps=1)]
+    for n, p in [(40, 3), (120, 6), (300, 10)]:
+        X, y = rand_problem(rng, n, p)
+        lams = oracle.lambda_max(X, y) * np.array([0.5, 0.1, 0.01])
+        ref = [oracle.simplex(X, y, lam)[0] for lam in lams]
+        for kw in settings:
+            r = oracle.fit_path(X, y, lams, opts=oracle.default_opts(**kw))
+            assert np.all((r["status"] & oracle.FIT_MAX_ITERS) == 0), kw
+            for l in range(len(lams)):
+                assert rel(r["f"][l], ref[l]) < 1e-10, (n, p, kw, l)

@@ -124,6 +124,7 @@ PINS = [
     ("test_plain_ccd_stalls_but_method_does_not", ()),
     ("test_chop_only_variant_is_not_always_optimal_but_never_worse", ()),
     ("test_lambda_path_warm_start_matches_cold_fits", ()),
+    ("test_exact_finish_makes_the_result_independent_of_chop_settings", ()),
     ("test_fit_batch_matches_single_fits", ()),
     ("test_active_set_gradient_matches_finite_differences", ()),
     ("test_simplex_matches_scipy_highs", ()),
