@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the option variants timed beside the headline (four-section chop, "
                          "chop off, looser descent)")
+    ap.add_argument("--no-cv", action="store_true",
+                    help="skip the cross-validation measurement (256 data sets x 5 folds x 16 lambdas)")
     ap.add_argument("--no-diff", action="store_true",
                     help="skip the forward + adjoint measurement (512 x 400/100 x 16)")
     ap.add_argument("--no-tune", action="store_true", help="library's default launch shape")
@@ -161,6 +163,13 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- our arm
+
+def batch_rows(batch, q):
+    """Design rows and targets of problem q of a batch whose slots are rows
+    of X (row_idx None)."""
+    o0, o1 = int(batch["offsets"][q]), int(batch["offsets"][q + 1])
+    return batch["X"][o0:o1], batch["y"][o0:o1]
+
 
 def row_updates(batch, counters, B):
     """Row-updates (one row's part in one 1-D weighted-median step) per fit:
@@ -576,6 +585,32 @@ def main():
                 "speedup": res[False][0] / res[True][0]}
         except Exception as ex:  # report, do not fail the bench line
             line["thread_per_fit"] = {"error": str(ex)}
+
+    # cross-validation of lambda: 256 data sets (500 rows x 16 columns, the
+    # differentiation recipe), 5 folds each, a 16-point path; one fit launch
+    # and one held-out-loss launch through the driver's public call, timed
+    # end to end (host index building and copies included)
+    if not args.no_cv and rank == 0:
+        try:
+            from paper_2510_15649_gb300 import cv
+            dcv = synth.diff(B=256, n=500, n_train=500, p=16, seed=8)["train"]
+            data = [batch_rows(dcv, q) for q in range(256)]
+            splits = [cv.kfold_splits(500, 5, seed=q) for q in range(256)]
+            cv.cross_validate_many(data[:8], splits[:8], L=16, device=dev)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res_cv = cv.cross_validate_many(data, splits, L=16, device=dev)
+            torch.cuda.synchronize()
+            t_cv = time.perf_counter() - t0
+            n_fits = 256 * 5 * 16
+            line["cv"] = {"workload": "256 data sets x 500 rows x 16 columns, 5-fold, 16 lambdas",
+                          "seconds": t_cv, "fits": n_fits, "fits_per_s": n_fits / t_cv,
+                          "data_sets_per_s": 256 / t_cv,
+                          "certified_fraction": float(np.mean([np.mean((r.status & 3) == 0)
+                                                               for r in res_cv]))}
+            log(f"cv {line['cv']}")
+        except Exception as ex:  # report, do not fail the bench line
+            line["cv"] = {"error": str(ex)}
 
     # continuous-batching server on Poisson arrivals (20k requests/s)
     if not args.no_serve and rank == 0:
