@@ -1,0 +1,29 @@
+"""Every repository path that README.md name in backticks
+exists (`csrc/...` is relative to the package), so the documents cannot
+point at files that were renamed or removed."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PKG = "paper_2510_15649_gb300"
+
+
+def _paths(doc):
+    s = open(os.path.join(ROOT, doc)).read()
+    found = set(re.findall(
+        r"`((?:tests|paper_2510_15649_gb300|profiles|include|oracle|csrc)/[A-Za-z0-9_./-]+?)"
+        r"(?:::[A-Za-z0-9_\[\]]+)?`", s))
+    found |= {p for p in re.findall(r"`([A-Za-z0-9_./-]+\.(?:py|cu|cuh|h|c|md))`", s) if "/" in p}
+    return sorted(found)
+
+
+@pytest.mark.parametrize("doc", ["DESIGN.md", "README.md"])
+def test_named_paths_exist(doc):
+    paths = _paths(doc)
+    assert paths, doc
+    missing = [p for p in paths
+               if not os.path.exists(os.path.join(ROOT, p)) and
+               not os.path.exists(os.path.join(ROOT, PKG, p))]
+    assert not missing, (doc, missing)
