@@ -27,3 +27,15 @@ def test_named_paths_exist(doc):
                if not os.path.exists(os.path.join(ROOT, p)) and
                not os.path.exists(os.path.join(ROOT, PKG, p))]
     assert not missing, (doc, missing)
+
+
+@pytest.mark.parametrize("doc", ["DESIGN.md", "README.md"])
+def test_named_tests_exist(doc):
+    s = open(os.path.join(ROOT, doc)).read()
+    refs = re.findall(r"`((?:tests/)?test_[A-Za-z0-9_]+\.py)::([A-Za-z0-9_]+)", s)
+    missing = []
+    for path, name in refs:
+        full = os.path.join(ROOT, path if path.startswith("tests/") else os.path.join("tests", path))
+        if not os.path.exists(full) or f"def {name}(" not in open(full).read():
+            missing.append(f"{path}::{name}")
+    assert not missing, (doc, missing)
