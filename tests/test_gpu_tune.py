@@ -75,3 +75,32 @@ def test_results_do_not_depend_on_work_order(ll):
     b = ll.fit(pr, lam, launch=ll.Launch(32, 0, 1))
     torch.cuda.synchronize()
     assert torch.equal(a["b"], b["b"]) and torch.equal(a["obj"], b["obj"])
+
+
+def permute_problems(batch, perm):
+    """The batch with its problems in the order `perm` (rows and targets
+    move with their problem; the shared design is unchanged)."""
+    off = batch["offsets"]
+    rows = [batch["row_idx"][off[q]:off[q + 1]] for q in perm]
+    ys = [batch["y"][off[q]:off[q + 1]] for q in perm]
+    lens = np.array([len(r) for r in rows], np.int64)
+    return dict(X=batch["X"], y=np.concatenate(ys), row_idx=np.concatenate(rows),
+                offsets=np.concatenate([[0], np.cumsum(lens)]).astype(np.int64),
+                p=np.asarray(batch["p"])[perm])
+
+
+def test_results_do_not_depend_on_problem_order(ll):
+    # each fit is one warp's own arithmetic: reordering the problems of a
+    # batch (same n_max, so the same launch shape) moves the results with
+    # them, bit for bit
+    import torch
+    batch, pr, lam = _setup(ll)
+    perm = np.random.default_rng(3).permutation(pr.B)
+    pb = permute_problems(batch, perm)
+    prp = ll.Problems.from_numpy(pb)
+    assert prp.n_max == pr.n_max
+    a = ll.fit(pr, lam)
+    b = ll.fit(prp, lam[torch.as_tensor(perm, device=lam.device)].contiguous())
+    torch.cuda.synchronize()
+    for k in ("b", "obj", "status"):
+        assert np.array_equal(a[k].cpu().numpy()[perm], b[k].cpu().numpy()), k
