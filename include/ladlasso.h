@@ -128,11 +128,10 @@ void ladlasso_default_opts(ladlasso_opts* o);
  *            0 = automatic (one warp per fit up to 8192 rows, else one
  *            512-thread block per fit), 32 = one warp per fit, 512 = one
  *            block per fit; any other value is LADLASSO_ERR_INVALID.  The
- *            automatic choice looks at n_max only: from P_cols = 159 one
- *            warp's share of shared memory holds fewer than 8192 rows, and
- *            n_max between that limit and 8192 returns LADLASSO_ERR_NOMEM
- *            unless 512 is asked for (ladlasso_launch_shape gives both
- *            limits; the autotuner offers only shapes that hold n_max).  The
+ *            automatic choice also takes one block per fit when one warp's
+ *            share of shared memory cannot hold n_max rows of P_cols columns
+ *            but a block's can (from P_cols = 159 a warp holds fewer than
+ *            8192 rows); ladlasso_launch_shape reports both limits.  The
  *            two shapes sum in different orders: results agree within the
  *            float32 tolerance, not bit for bit
  * fits_per_block  one-warp shape: at most this many fits per thread block

@@ -2200,9 +2200,19 @@ int fit_block_max_rows(int G, int P) {
 // a warp's share of shared memory, else a block per fit.
 int fit_block_group(int n_max) { return n_max <= 8192 ? 32 : kBlockG; }
 
-// Group size a call asks for (dims->group_threads), 0 when invalid.
+// Group size a call asks for (dims->group_threads), 0 when invalid.  The
+// automatic choice (0) also takes the block shape when a warp's share of
+// shared memory cannot hold n_max rows of these columns but a block's can
+// (wide problems: from about 160 columns a warp holds fewer than 8192 rows).
 int launch_group(const ladlasso_dims* d) {
-  if (d->group_threads == 0) return fit_block_group(d->n_max);
+  if (d->group_threads == 0) {
+    int G = fit_block_group(d->n_max);
+    if (G == 32 && d->P_cols >= 1 && d->P_cols <= kMaxP &&
+        d->n_max > fit_block_max_rows(32, d->P_cols) &&
+        d->n_max <= fit_block_max_rows(kBlockG, d->P_cols))
+      G = kBlockG;
+    return G;
+  }
   return d->group_threads == 32 || d->group_threads == kBlockG ? d->group_threads : 0;
 }
 

@@ -61,6 +61,12 @@ def test_launch_shape_is_host_only_and_consistent():
     # n_max beyond the one-warp limit with an explicit one-warp request
     g4, f4, m4 = ll.launch_shape(Pr(32, 50000), ll.Launch(32, 0))
     assert g4 == 32 and m4 < 50000
+    # wide problems: the automatic shape takes one block per fit when a
+    # warp's share of shared memory cannot hold n_max rows but a block's can
+    g5, _, m5 = ll.launch_shape(Pr(180, 7000))
+    assert g5 == 512 and m5 >= 7000
+    assert ll.launch_shape(Pr(180, 7000), ll.Launch(32, 0))[2] < 7000
+    assert ll.launch_shape(Pr(180, 5000))[0] == 32  # a warp still holds it
     # invalid shapes
     import pytest
     with pytest.raises(ll.LadLassoError):
