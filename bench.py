@@ -633,13 +633,22 @@ def main():
         import oracle
         oracle.build()
         cores = os.cpu_count() or 1
-        nq = max(8, min(48, 2 * cores))
         lh = lam.cpu().numpy().astype(np.float64)
-        t0 = time.perf_counter()
-        r = oracle.fit_batch(batch, lh, problems=np.arange(nq), nthreads=cores)
-        dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": nq * L / dt, "unit": "fits/s", "cores": r["threads"],
-                                "kind": "oracle", "sample": f"problems 0..{nq - 1} x {L} lambdas"}
+        # problems in order, a chunk of about two per core at a time, until
+        # at least 10 s of CPU work has been timed (a bounded sample)
+        chunk = max(8, 2 * cores)
+        done, dt, used = 0, 0.0, 1
+        while done < B and dt < 10.0:
+            qs = np.arange(done, min(B, done + chunk))
+            t0 = time.perf_counter()
+            r = oracle.fit_batch(batch, lh, problems=qs, nthreads=cores)
+            dt += time.perf_counter() - t0
+            done += len(qs)
+            used = r["threads"]
+        line["cpu_baseline"] = {"value": done * L / dt, "unit": "fits/s", "cores": used,
+                                "kind": "oracle",
+                                "sample": f"problems 0..{done - 1} x {L} lambdas of the workload "
+                                          f"({dt:.1f} s, chunks of {chunk} problems)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
