@@ -447,7 +447,11 @@ def test_exact_finish_makes_the_result_independent_of_chop_settings():
     # the dense simplex
     rng = np.random.default_rng(21)
     settings = [dict(), dict(chop=0), dict(chop_sections=4), dict(tol_move=1e-3),
-                dict(chop=0, tol_move=1e-3), dict(chop_max_probes=2, probe_max_sweeps=1)]
+                dict(chop=0, tol_move=1e-3), dict(chop_max_probes=2, probe_max_sweeps=1),
+                # the chop constants proposed as readings of Sections 3.4-3.5
+                # before the exact finish existed: a bracket of max(1, |b_k|),
+                # up to 40 extensions, range 1e-12 or 80 probes
+                dict(chop_bracket=1.0, chop_max_extend=40, chop_tol=1e-12, chop_max_probes=80)]
     for n, p in [(40, 3), (120, 6), (300, 10)]:
         X, y = rand_problem(rng, n, p)
         lams = oracle.lambda_max(X, y) * np.array([0.5, 0.1, 0.01])
