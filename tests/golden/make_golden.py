@@ -17,7 +17,8 @@ import oracle  # noqa: E402
 from paper_2510_15649_gb300 import synth  # noqa: E402
 
 
-def main():
+def compute() -> dict:
+    """The stored values, computed afresh by the oracle."""
     t = synth.tiny()
     X = t["X"].astype(np.float64)
     y = t["y"].astype(np.float64)
@@ -29,6 +30,11 @@ def main():
                b_star=list(map(float, bb)), n_optimal_vertices=nd,
                F_simplex=fs, lambda_max=lmax,
                source="oracle.brute_force (Section 3.2) / oracle.simplex (Section 3.1)")
+    return out
+
+
+def main():
+    out = compute()
     with open(os.path.join(HERE, "tiny_fit.json"), "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps(out, indent=1))

@@ -56,6 +56,26 @@ def test_tiny_golden_brute_simplex_method_agree():
     assert gap < 1e-9 and info["unique"]
 
 
+def test_golden_file_is_what_its_script_computes():
+    # the stored expected values come only from tests/golden/make_golden.py,
+    # which calls only oracle/: recomputing gives the stored file
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "make_golden", os.path.join(HERE, "golden", "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    fresh = mg.compute()
+    stored = json.load(open(os.path.join(HERE, "golden", "tiny_fit.json")))
+    assert set(fresh) == set(stored)
+    for k, v in stored.items():
+        if isinstance(v, float):
+            assert rel(fresh[k], v) < 1e-12, k
+        elif isinstance(v, list):
+            np.testing.assert_allclose(fresh[k], v, rtol=1e-12, atol=1e-14)
+        else:
+            assert fresh[k] == v, k
+
+
 def test_simplex_matches_scipy_highs():
     linprog = pytest.importorskip("scipy.optimize").linprog
     rng = np.random.default_rng(11)
