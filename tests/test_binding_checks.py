@@ -95,3 +95,13 @@ def test_result_buffers_are_checked():
         ll._check_out(dict(b=good["b"], obj=good["obj"]), B, L, P, dev)
     ll._check_out(dict(b=good["b"], basis=good["basis"]), B, L, P, dev, required=("b", "basis"))
     assert np.all(good["b"].numpy() == 0)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    # no CPU fallback: without the built library every call raises
+    monkeypatch.setattr(ll, "_lib", None)
+    monkeypatch.setattr(ll, "LIB_PATH", ll.LIB_PATH + ".missing")
+    with pytest.raises(ll.LadLassoError, match="not built"):
+        ll.lib()
+    with pytest.raises(ll.LadLassoError, match="not built"):
+        ll.default_opts()
