@@ -122,7 +122,10 @@ void ladlasso_default_opts(ladlasso_opts* o);
  *            descent + chop, kilocycles in basis/polish work (the last four
  *            are counted by the batched kernel only, else 0)
  * workspace  device scratch of at least ladlasso_workspace_size(...) bytes,
- *            256-byte aligned; contents need not be initialised
+ *            256-byte aligned; contents need not be initialised.  It serves
+ *            one call at a time (it holds the call's work counter and
+ *            gathered designs): calls that may run at the same time, on
+ *            different streams, need workspaces of their own
  * opts     host pointer or NULL for defaults
  * group_threads   launch shape of ladlasso_fit_batched (and _noalloc):
  *            0 = automatic (one warp per fit up to 8192 rows, else one
