@@ -24,6 +24,7 @@ SOURCES = ["api.cu", "fit_block.cu", "fit_thread.cu", "aux_kernels.cu", "backwar
 
 
 def nvcc() -> str:
+    """Path of the CUDA compiler."""
     for c in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if c and os.path.exists(c):
             return c
@@ -39,6 +40,9 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+    """Compile the CUDA sources for sm_103a (one nvcc per translation unit,
+    in parallel) and link libladlasso.so in the package directory, unless
+    it is newer than every source and the header.  Returns its path."""
     if not force and not _stale():
         return OUT
     os.makedirs(BUILD, exist_ok=True)

@@ -23,6 +23,7 @@ from . import ladlasso as ll
 
 @dataclass
 class CVResult:
+    """Cross-validation of one data set along its lambda path."""
     lambdas: np.ndarray    # [L] shared path
     loss: np.ndarray       # [S, L] held-out LAD loss per split
     mean_loss: np.ndarray  # [L] mean over splits of the per-row held-out loss
@@ -32,6 +33,7 @@ class CVResult:
 
     @property
     def best_lambda(self) -> float:
+        """The lambda with the smallest mean held-out loss."""
         return float(self.lambdas[self.best])
 
 

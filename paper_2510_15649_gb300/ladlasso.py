@@ -26,6 +26,8 @@ FIT_OK, FIT_MAX_ITERS, FIT_BAD_INPUT, FIT_NONUNIQUE = 0, 1, 2, 4
 
 
 class Opts(C.Structure):
+    """ladlasso_opts: the method's options (include/ladlasso.h); fill with
+    default_opts(**overrides)."""
     _fields_ = [("tol_move", C.c_float), ("max_sweeps", C.c_int32), ("chop", C.c_int32),
                 ("chop_bracket", C.c_float), ("chop_tol", C.c_float),
                 ("chop_max_probes", C.c_int32), ("chop_max_extend", C.c_int32),
@@ -35,6 +37,8 @@ class Opts(C.Structure):
 
 
 class Dims(C.Structure):
+    """ladlasso_dims: sizes and side arrays of one call; built by
+    Problems.dims()."""
     _fields_ = [("B", C.c_int32), ("P_cols", C.c_int32), ("L", C.c_int32), ("n_max", C.c_int32),
                 ("ldX", C.c_int64), ("rows_X", C.c_int64), ("total_rows", C.c_int64),
                 ("p", C.c_void_p), ("n_rows", C.c_void_p), ("b_init", C.c_void_p), ("fit_status", C.c_void_p),
@@ -45,7 +49,8 @@ class Dims(C.Structure):
 
 
 class LadLassoError(RuntimeError):
-    pass
+    """A negative status from the library, or an argument the binding
+    refuses before calling it."""
 
 
 SYMBOLS = ["ladlasso_default_opts", "ladlasso_workspace_size", "ladlasso_lambda_max",
@@ -96,6 +101,7 @@ def _check(rc: int):
 
 
 def default_opts(**kw) -> Opts:
+    """The library's default options with the given fields overridden."""
     o = Opts()
     lib().ladlasso_default_opts(C.byref(o))
     for k, v in kw.items():
@@ -227,10 +233,13 @@ class Problems:
 
     @property
     def B(self) -> int:
+        """Number of problems (offsets has B + 1 entries)."""
         return int(self.offsets.numel()) - 1
 
     def dims(self, L: int, workspace: torch.Tensor, opts: Opts | None = None, b_init=None,
              status=None, basis=None, counters=None) -> Dims:
+        """ladlasso_dims for a call on this problem set with path length L,
+        after checking every tensor the library will read."""
         _check_problems(self)
         d = Dims()
         d.B, d.P_cols, d.L, d.n_max = self.B, self.P, L, self.n_max
@@ -250,6 +259,7 @@ class Problems:
 
 
 def workspace_bytes(pr: Problems, L: int = 1) -> int:
+    """Bytes of workspace the calls on `pr` need (ladlasso_workspace_size)."""
     n = lib().ladlasso_workspace_size(pr.B, pr.P, int(pr.y.numel()), L)
     if n == 0:
         raise LadLassoError("invalid sizes for workspace")
@@ -263,6 +273,9 @@ def workspace(pr: Problems, L: int = 1) -> torch.Tensor:
 
 
 def lambda_max(pr: Problems, ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Per problem the smallest lambda at which b = 0 is optimal,
+    max_j |x_j . sign(y)| over its rows and columns; NaN for a problem with
+    bad input.  Returns [B] float32 on the device."""
     _check_problems(pr)
     ws = workspace(pr) if ws is None else ws
     _need(ws, "workspace", torch.uint8, pr.X.device)
@@ -275,6 +288,8 @@ def lambda_max(pr: Problems, ws: torch.Tensor | None = None, stream=None) -> tor
 
 
 def lambda_path(lmax: torch.Tensor, L: int, ratio: float = 1e-3, stream=None) -> torch.Tensor:
+    """Geometric paths lmax[q] * ratio^(l / (L - 1)), l = 0..L-1 (lmax alone
+    when L = 1).  Returns [B, L] float32 on the device."""
     B = int(lmax.numel())
     if lmax.device.type != "cuda":
         raise LadLassoError(f"lmax must be in CUDA device memory (it is on {lmax.device})")

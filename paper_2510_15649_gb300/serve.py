@@ -43,6 +43,7 @@ def admission_offsets(slots: np.ndarray, cap: int, S: int) -> np.ndarray:
 
 @dataclass
 class Result:
+    """One served request: its fitted path and when it arrived and finished."""
     rid: int
     b: np.ndarray          # [L, p]
     obj: np.ndarray        # [L]
@@ -54,6 +55,7 @@ class Result:
 
 @dataclass
 class ServeStats:
+    """Counts and latencies of one Server.run."""
     completed: int = 0
     fits: int = 0          # fits with valid input (status without BAD_INPUT)
     bad_fits: int = 0
@@ -64,6 +66,7 @@ class ServeStats:
     queued_max: int = 0
 
     def summary(self) -> dict:
+        """Requests, fits, fits/s and p50/p99 latency (ms) as a dict."""
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
         return dict(requests=self.completed, fits=self.fits, bad_fits=self.bad_fits, steps=self.steps,
                     seconds=self.wall, fits_per_s=self.fits / max(self.wall, 1e-9),
