@@ -435,7 +435,12 @@ def main():
                         "selection_passes_per_select": float(cnt[..., 4].sum() / max(1, cnt[..., 5].sum())),
                         "ccd_point_optimal": float(np.mean((fl & 1) != 0)),
                         "chop_ran": float(np.mean((fl & 2) != 0)),
-                        "chop_point_optimal": float(np.mean((fl & 4) != 0))}
+                        "chop_point_optimal": float(np.mean((fl & 4) != 0)),
+                        # SM cycles per fit spent in descent + chop and in the
+                        # basis / polish work (counter slots 6 and 7)
+                        "descent_chop_cycle_share": float(
+                            cnt[..., 6].astype(np.float64).sum()
+                            / max(1.0, cnt[..., 6:8].astype(np.float64).sum()))}
 
     # the same fits under option variants that the exact finish makes
     # result-neutral (the four-section chop; chop = 0: the polish straight
