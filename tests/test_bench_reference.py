@@ -53,3 +53,12 @@ def test_reference_other_ranks_print_nothing():
               env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert pr.returncode == 0, pr.stderr[-2000:]
     assert not [ln for ln in pr.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_bench_arguments_parse():
+    pr = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], cwd=ROOT,
+                        capture_output=True, text=True, timeout=300)
+    assert pr.returncode == 0, pr.stderr[-2000:]
+    for flag in ("--gpus", "--steps", "--warmup", "--impl", "--no-variants", "--no-cv",
+                 "--no-large", "--no-diff", "--no-serve", "--launch"):
+        assert flag in pr.stdout, flag
