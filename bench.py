@@ -632,6 +632,22 @@ def main():
             log(f"serve {line['serve']}")
         except Exception as ex:
             line["serve"] = {"error": str(ex)}
+        # the same trace and total slot count in slot classes sized to the
+        # request mix (58 % of requests have n <= 500, 83 % n <= 2000)
+        try:
+            from paper_2510_15649_gb300.serve import ClassedServer
+            classes = [(1280, 500, 64), (512, 2000, 64), (256, 5000, 64)]
+            ClassedServer(classes, L=8, device=dev).run(trace[:64])  # warm-up
+            csrv = ClassedServer(classes, L=8, device=dev)
+            _, cst = csrv.run(trace)
+            if isinstance(line.get("serve"), dict) and "error" not in line["serve"]:
+                line["serve"]["slot_classes"] = dict(
+                    cst.summary(), classes="slots x rows (64 columns): 1280 x 500, 512 x 2000, "
+                                           "256 x 5000")
+            log(f"serve slot classes {cst.summary()}")
+        except Exception as ex:
+            if isinstance(line.get("serve"), dict):
+                line["serve"]["slot_classes"] = {"error": str(ex)}
 
     # CPU oracle baseline on a bounded sample
     if rank == 0 and not args.no_cpu_baseline:

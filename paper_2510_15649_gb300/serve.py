@@ -16,7 +16,10 @@ the request loop on the host:
             their slot; latency = arrival -> result on the host
 
 Requests that arrive while others are on the GPU join at the next step, so
-work from different requests overlaps inside every launch.  A request's
+work from different requests overlaps inside every launch.  `ClassedServer`
+runs the same loop over several pools of different slot sizes (slot
+classes): a request takes a slot of the smallest class that holds it, so
+short requests do not reserve a long request's shared memory.  A request's
 results equal those of fitting it alone along the same path (same kernel,
 same per-fit arithmetic).  All arithmetic runs in the CUDA library; this
 module only moves data and keeps the schedule.
@@ -140,81 +143,142 @@ class Server:
         self.b[torch.from_numpy(ss).to(self.dev)] = 0.0
         return slots
 
+    # ---------------------------------------------------------------- step
+    def _active(self) -> np.ndarray:
+        return np.nonzero(self.h_rid >= 0)[0]
+
+    def _launch(self) -> bool:
+        """One fit launch advancing every active slot by one path position
+        (warm-started in place); False when no slot is active."""
+        active = self._active()
+        if len(active) == 0:
+            return False
+        lam = np.full(self.S, np.nan, np.float32)
+        lam[active] = self.h_lam[active, self.h_pos[active]]
+        self.lam_step.copy_(torch.from_numpy(lam).reshape(self.S, 1), non_blocking=True)
+        ll.fit(self.pr, self.lam_step, b_init=self.b, ws=self.ws, opts=self.opts,
+               out=dict(b=self.b, obj=self.obj, status=self.status))
+        return True
+
+    def _collect(self, st: ServeStats, arrive: dict, results: list) -> None:
+        """After a launch: copy the step's results, advance the active slots,
+        retire the requests whose path is done."""
+        active = self._active()
+        bh = self.b.cpu().numpy()[:, 0]
+        oh = self.obj.cpu().numpy()[:, 0]
+        sh = self.status.cpu().numpy()[:, 0]
+        pos = self.h_pos[active]
+        self.h_b[active, pos] = bh[active]
+        self.h_obj[active, pos] = oh[active]
+        self.h_st[active, pos] = sh[active]
+        self.h_pos[active] += 1
+        valid = (sh[active] & 2) == 0
+        st.fits += int(valid.sum())
+        st.bad_fits += int((~valid).sum())
+        done = active[self.h_pos[active] >= self.L]
+        tnow = time.perf_counter()
+        for s in done:
+            rid = int(self.h_rid[s])
+            p = int(self.h_p[s])
+            results.append(Result(rid=rid, b=self.h_b[s, :, :p].copy(),
+                                  obj=self.h_obj[s].copy(), status=self.h_st[s].copy(),
+                                  lambdas=self.h_lam[s].copy(), t_arrival=arrive[rid],
+                                  t_done=tnow))
+            st.latencies.append(tnow - arrive[rid])
+            self.used -= int(self.h_n[s]) * p
+            self.h_rid[s] = -1
+            self.h_n[s] = 0
+            self.free.append(int(s))
+            st.completed += 1
+        if len(done):
+            self.n_rows.copy_(torch.from_numpy(self.h_n), non_blocking=True)
+
     # ---------------------------------------------------------------- run
     def run(self, trace: list, time_scale: float = 1.0) -> tuple:
         """Serve `trace` (list of dicts with t, X, y), arrivals replayed in
         real time scaled by time_scale.  Returns (results, ServeStats)."""
-        st = ServeStats()
-        results = []
-        t0 = time.perf_counter()
-        arrive = {i: t0 + trace[i]["t"] * time_scale for i in range(len(trace))}
-        queue = []
-        nxt = 0
-        while nxt < len(trace) or queue or np.any(self.h_rid >= 0):
-            now = time.perf_counter()
-            while nxt < len(trace) and arrive[nxt] <= now:
-                queue.append(nxt)
-                nxt += 1
-            st.queued_max = max(st.queued_max, len(queue))
-            adm, adm_ids, extra = [], [], 0
-            while queue and len(adm) < len(self.free):
-                i = queue[0]
-                n, p = trace[i]["X"].shape
-                if n > self.cap or p > self.P:
-                    raise ValueError(f"request {i} ({n}x{p}) exceeds the slot capacity")
-                if n * p > self.budget:
-                    raise ValueError(f"request {i} ({n}x{p}) exceeds the memory budget "
-                                     f"of {self.budget} floats on its own")
-                if self.used + extra + n * p > self.budget:
-                    break  # device-memory admission: wait for requests to retire
-                queue.pop(0)
-                adm.append(trace[i])
-                adm_ids.append(i)
-                extra += n * p
-            if adm:
+        return serve_pools([self], trace, time_scale, self.budget)
+
+
+def serve_pools(pools: list, trace: list, time_scale: float, budget: int) -> tuple:
+    """The request loop over one or more slot pools (ordered from the
+    smallest slot capacity up).  Arrivals queue in order; the queue's head
+    takes a free slot of the first pool whose slots hold it (cap rows, P
+    columns) while the active requests' n * p stays within `budget`.  Each
+    step launches every pool with active slots, then collects their
+    results.  Returns (results, ServeStats)."""
+    st = ServeStats()
+    results = []
+    t0 = time.perf_counter()
+    arrive = {i: t0 + trace[i]["t"] * time_scale for i in range(len(trace))}
+    queue = []
+    nxt = 0
+    while nxt < len(trace) or queue or any(len(pl._active()) for pl in pools):
+        now = time.perf_counter()
+        while nxt < len(trace) and arrive[nxt] <= now:
+            queue.append(nxt)
+            nxt += 1
+        st.queued_max = max(st.queued_max, len(queue))
+        plan = [([], []) for _ in pools]
+        free_left = [len(pl.free) for pl in pools]
+        used = sum(pl.used for pl in pools)
+        extra = 0
+        while queue:
+            i = queue[0]
+            n, p = trace[i]["X"].shape
+            holders = [k for k, pl in enumerate(pools) if n <= pl.cap and p <= pl.P]
+            if not holders:
+                raise ValueError(f"request {i} ({n}x{p}) exceeds the slot capacity")
+            if n * p > budget:
+                raise ValueError(f"request {i} ({n}x{p}) exceeds the memory budget "
+                                 f"of {budget} floats on its own")
+            k = next((k for k in holders if free_left[k] > 0), None)
+            if k is None:
+                break  # every pool that holds it is full: wait for a slot
+            if used + extra + n * p > budget:
+                break  # device-memory admission: wait for requests to retire
+            queue.pop(0)
+            plan[k][0].append(trace[i])
+            plan[k][1].append(i)
+            free_left[k] -= 1
+            extra += n * p
+        for pl, (reqs, rids) in zip(pools, plan):
+            if reqs:
                 with ll._nvtx("serve_admit"):
-                    self._admit(adm, adm_ids)
-            active = np.nonzero(self.h_rid >= 0)[0]
-            if len(active) == 0:
-                if nxt < len(trace):  # idle until the next arrival
-                    time.sleep(max(0.0, min(arrive[nxt] - time.perf_counter(), 1e-3)))
-                continue
-            st.max_active = max(st.max_active, len(active))
-            lam = np.full(self.S, np.nan, np.float32)
-            lam[active] = self.h_lam[active, self.h_pos[active]]
-            self.lam_step.copy_(torch.from_numpy(lam).reshape(self.S, 1), non_blocking=True)
-            with ll._nvtx("serve_step"):
-                ll.fit(self.pr, self.lam_step, b_init=self.b, ws=self.ws, opts=self.opts,
-                       out=dict(b=self.b, obj=self.obj, status=self.status))
-                st.steps += 1
-                # every active request advanced one position; copy this step's results
-                bh = self.b.cpu().numpy()[:, 0]
-                oh = self.obj.cpu().numpy()[:, 0]
-                sh = self.status.cpu().numpy()[:, 0]
-            pos = self.h_pos[active]
-            self.h_b[active, pos] = bh[active]
-            self.h_obj[active, pos] = oh[active]
-            self.h_st[active, pos] = sh[active]
-            self.h_pos[active] += 1
-            valid = (sh[active] & 2) == 0
-            st.fits += int(valid.sum())
-            st.bad_fits += int((~valid).sum())
-            done = active[self.h_pos[active] >= self.L]
-            tnow = time.perf_counter()
-            for s in done:
-                rid = int(self.h_rid[s])
-                p = int(self.h_p[s])
-                results.append(Result(rid=rid, b=self.h_b[s, :, :p].copy(),
-                                      obj=self.h_obj[s].copy(), status=self.h_st[s].copy(),
-                                      lambdas=self.h_lam[s].copy(), t_arrival=arrive[rid],
-                                      t_done=tnow))
-                st.latencies.append(tnow - arrive[rid])
-                self.used -= int(self.h_n[s]) * p
-                self.h_rid[s] = -1
-                self.h_n[s] = 0
-                self.free.append(int(s))
-                st.completed += 1
-            if len(done):
-                self.n_rows.copy_(torch.from_numpy(self.h_n), non_blocking=True)
-        st.wall = time.perf_counter() - t0
-        return results, st
+                    pl._admit(reqs, rids)
+        n_active = sum(len(pl._active()) for pl in pools)
+        if n_active == 0:
+            if nxt < len(trace):  # idle until the next arrival
+                time.sleep(max(0.0, min(arrive[nxt] - time.perf_counter(), 1e-3)))
+            continue
+        st.max_active = max(st.max_active, n_active)
+        with ll._nvtx("serve_step"):
+            launched = [pl for pl in pools if pl._launch()]
+            st.steps += 1
+            for pl in launched:
+                pl._collect(st, arrive, results)
+    st.wall = time.perf_counter() - t0
+    return results, st
+
+
+class ClassedServer:
+    """Slot classes: one pool per (slots, cap, P) class, ordered by slot
+    size.  A request takes a slot of the smallest class that holds it (a
+    larger class when that one is full), so short requests do not reserve a
+    long request's shared memory and more fits run at once; every step
+    launches each class with active slots.  `budget_floats` bounds the total
+    n * p of the active requests over all classes."""
+
+    def __init__(self, classes: list, L: int = 8, ratio: float = 1e-3,
+                 budget_floats: int | None = None, device="cuda", opts: ll.Opts | None = None):
+        cl = sorted(classes, key=lambda c: (c[1] * c[2], c[1], c[2]))
+        if not cl:
+            raise ValueError("no slot classes")
+        self.pools = [Server(slots=sl, cap=cap, P=P, L=L, ratio=ratio, device=device, opts=opts)
+                      for sl, cap, P in cl]
+        self.budget = budget_floats if budget_floats is not None else \
+            sum(sl * cap * P for sl, cap, P in cl)
+
+    def run(self, trace: list, time_scale: float = 1.0) -> tuple:
+        """As Server.run, over every class."""
+        return serve_pools(self.pools, trace, time_scale, self.budget)

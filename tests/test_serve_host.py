@@ -184,3 +184,81 @@ def test_request_beyond_the_memory_budget_is_refused_not_queued_forever(fake):
     # exactly at the budget it is served
     results, st = Server(slots=2, cap=300, P=8, L=2, budget_floats=400, device="cpu").run([req])
     assert st.completed == 1
+
+
+# ------------------------------------------------------------------ slot classes
+
+
+def _record_admissions(pools, log):
+    for pl in pools:
+        orig = pl._admit
+
+        def wrapped(reqs, rids, pl=pl, orig=orig):
+            out = orig(reqs, rids)
+            # the smallest class's free slots when this admission happens
+            # (each round admits the classes smallest first)
+            log.append((pl.cap, pl.P, list(rids), len(pools[0].free),
+                        sum(q.used for q in pools)))
+            return out
+        pl._admit = wrapped
+
+
+def test_slot_classes_serve_every_request_from_a_class_that_holds_it(fake):
+    from paper_2510_15649_gb300.serve import ClassedServer
+    fake()
+    trace = _trace(n=40, seed=7)
+    L = 3
+    srv = ClassedServer([(2, 300, 8), (3, 100, 8)], L=L, device="cpu")
+    assert [pl.cap for pl in srv.pools] == [100, 300]  # smallest class first
+    log = []
+    _record_admissions(srv.pools, log)
+    results, st = srv.run(trace, time_scale=0.0)  # every request waiting at once
+    assert st.completed == len(trace) and st.bad_fits == 0
+    assert sorted(r.rid for r in results) == list(range(len(trace)))
+    where = {}
+    for cap, P, rids, _, _ in log:
+        for rid in rids:
+            n, p = trace[rid]["X"].shape
+            assert n <= cap and p <= P
+            where[rid] = cap
+    small = [i for i, r in enumerate(trace) if r["X"].shape[0] <= 100]
+    assert small and any(where[i] == 100 for i in small)
+    # a short request in the large class only while the small class was full
+    fallbacks = 0
+    for cap, P, rids, small_free, _ in log:
+        if cap == 300 and any(trace[rid]["X"].shape[0] <= 100 for rid in rids):
+            assert small_free == 0
+            fallbacks += 1
+    assert fallbacks > 0  # with every request waiting, the small class overflows
+    for r in results:  # own data, own path, warm starts, as with one pool
+        X, y = trace[r.rid]["X"], trace[r.rid]["y"]
+        lmax = np.abs(X.T @ np.sign(y)).max()
+        np.testing.assert_allclose(r.lambdas[0], lmax, rtol=1e-5)
+        for l in range(L):
+            assert np.all(r.b[l] == l + 1.0)
+
+
+def test_slot_classes_share_one_memory_budget(fake):
+    from paper_2510_15649_gb300.serve import ClassedServer
+    fake()
+    trace = _trace(n=24, seed=8)
+    budget = int(1.5 * max(r["X"].size for r in trace))
+    srv = ClassedServer([(4, 300, 8), (4, 100, 8)], L=2, budget_floats=budget, device="cpu")
+    log = []
+    _record_admissions(srv.pools, log)
+    results, st = srv.run(trace, time_scale=0.0)
+    assert st.completed == len(trace)
+    assert max(u for *_, u in log) <= budget
+    assert all(pl.used == 0 for pl in srv.pools)
+
+
+def test_slot_classes_refuse_a_request_no_class_holds(fake):
+    from paper_2510_15649_gb300.serve import ClassedServer
+    fake()
+    rng = np.random.default_rng(3)
+    big = dict(t=0.0, X=rng.standard_normal((301, 4)).astype(np.float32),
+               y=rng.standard_normal(301).astype(np.float32))
+    with pytest.raises(ValueError, match="slot capacity"):
+        ClassedServer([(2, 100, 8), (2, 300, 8)], L=2, device="cpu").run([big])
+    with pytest.raises(ValueError):
+        ClassedServer([], device="cpu")
