@@ -291,6 +291,45 @@ def test_invariances():
     assert rel(rd["f"][0], fd) < 1e-11
 
 
+def test_sign_symmetries_and_a_zero_column():
+    rng = np.random.default_rng(23)
+    X, y = rand_problem(rng, 70, 5)
+    lam = 0.2 * oracle.lambda_max(X, y)
+    b0 = oracle.fit_path(X, y, [lam])["b"][0]
+    # F(b; X, y) with column j negated equals F with b_j negated
+    Xf = X.copy()
+    Xf[:, 2] *= -1
+    bf = oracle.fit_path(Xf, y, [lam])["b"][0]
+    np.testing.assert_allclose(bf, b0 * np.array([1, 1, -1, 1, 1]), atol=1e-9)
+    # F(b; X, -y) = F(-b; X, y)
+    np.testing.assert_allclose(oracle.fit_path(X, -y, [lam])["b"][0], -b0, atol=1e-9)
+    # a column of zeros gets a zero coefficient and changes nothing else
+    Xz = np.hstack([X[:, :3], np.zeros((70, 1)), X[:, 3:]])
+    bz = oracle.fit_path(Xz, y, [lam])["b"][0]
+    assert bz[3] == 0.0
+    np.testing.assert_allclose(np.delete(bz, 3), b0, atol=1e-9)
+
+
+def test_optimum_along_lambda_is_nondecreasing_and_concave():
+    # F*(lambda) = min_b (sum |r| + lambda |b|_1) is a minimum of functions
+    # affine in lambda: nondecreasing and concave; the minimiser's |b|_1 is
+    # its slope, so it does not increase with lambda.  Values from the dense
+    # simplex, coefficients from the method's path.
+    rng = np.random.default_rng(25)
+    X, y = rand_problem(rng, 50, 4)
+    lams = oracle.lambda_max(X, y) * np.linspace(0.02, 1.2, 13)
+    f = np.array([oracle.simplex(X, y, lam)[0] for lam in lams])
+    assert np.all(np.diff(f) >= -1e-9)
+    slopes = np.diff(f) / np.diff(lams)
+    assert np.all(np.diff(slopes) <= 1e-9)
+    path = oracle.fit_path(X, y, lams[::-1])  # descending, warm-started
+    l1 = np.abs(path["b"]).sum(axis=1)[::-1]
+    assert np.all(np.diff(l1) <= 1e-9)
+    np.testing.assert_allclose(path["f"][::-1], f, rtol=1e-10)
+    # between grid points the slope of F* brackets |b|_1
+    assert np.all(slopes <= l1[:-1] + 1e-9) and np.all(slopes >= l1[1:] - 1e-9)
+
+
 # ---------------------------------------------------------------- certificate
 
 def test_certificate_detects_suboptimal_points():
