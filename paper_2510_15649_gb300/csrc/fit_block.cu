@@ -3,7 +3,8 @@
 //   G = 32   one warp per fit, NW independent warps per block, no block
 //            barriers; each 1-D step is one fused pass over the rows (below)
 //            reading the column from a shared-memory double buffer
-//   G > 32   one block per fit (long problems): the same windowed passes,
+//   G > 32   one block per fit (long problems, or wide ones whose rows a
+//            warp's share of shared memory cannot hold): the same windowed passes,
 //            the warps classifying interleaved row chunks into per-warp
 //            sub-buffers, the columns streamed from the gathered design
 //
