@@ -424,6 +424,14 @@ def main():
                             f"{launch.group_threads}x{launch.fits_per_block}/o{launch.work_order}"),
                         "kernel": "fit_block_kernel", "kernel_ms": 1e3 * t_fit,
                         "row_updates_per_launch": ru}
+    # the same kernel against shared-memory bandwidth: 12 algorithmic bytes
+    # per row-update (column element and residual read, residual write)
+    # against 32 banks x 4 B per clock per SM
+    smem_peak = 152 * 32 * 4 * mhz * 1e6 / 1e9
+    smem_ach = 12.0 * ru / t_fit / 1e9
+    line["roofline_smem"] = {"bound": "smem", "achieved": smem_ach, "peak": smem_peak,
+                             "unit": "GB/s", "frac": smem_ach / smem_peak,
+                             "bytes_per_row_update": 12, "kernel": "fit_block_kernel"}
     line["clocks"] = clk_s
     # per-fit counters of the last timed step (work the method did)
     def pct(a):
