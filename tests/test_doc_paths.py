@@ -1,6 +1,7 @@
 """Every repository path that README.md name in backticks
 exists (`csrc/...` is relative to the package), so the documents cannot
 point at files that were renamed or removed."""
+import glob
 import os
 import re
 
@@ -39,3 +40,14 @@ def test_named_tests_exist(doc):
         if not os.path.exists(full) or f"def {name}(" not in open(full).read():
             missing.append(f"{path}::{name}")
     assert not missing, (doc, missing)
+
+
+@pytest.mark.parametrize("doc", sorted(os.path.relpath(p, ROOT)
+                                       for p in glob.glob(os.path.join(ROOT, "profiles", "*.md"))))
+def test_profile_summaries_name_committed_files_only(doc):
+    s = open(os.path.join(ROOT, doc)).read()
+    assert "_work/" not in s and "gpurun" not in s, doc
+    assert "--clock-control none" in s, doc  # every capture left the clocks alone
+    assert "bench.py" in s, doc              # the command runs a committed script
+    for p in _paths(doc):
+        assert os.path.exists(os.path.join(ROOT, p)) or os.path.exists(os.path.join(ROOT, PKG, p)), p
