@@ -164,6 +164,18 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- our arm
 
+def log2_histogram(a) -> dict:
+    """Counts of the values of `a` in the buckets [0], [1], [2, 3], [4, 7],
+    ... (powers of two); edges are the buckets' lower ends."""
+    a = np.asarray(a).ravel()
+    top = int(a.max()) if a.size else 0
+    edges = [0, 1]
+    while edges[-1] <= top:
+        edges.append(edges[-1] * 2)
+    counts = np.histogram(a, bins=np.array(edges, dtype=np.float64) - 0.5)[0]
+    return {"lower_edges": edges[:-1], "counts": counts.astype(int).tolist()}
+
+
 def batch_rows(batch, q):
     """Design rows and targets of problem q of a batch whose slots are rows
     of X (row_idx None)."""
@@ -448,7 +460,10 @@ def main():
                         # basis / polish work (counter slots 6 and 7)
                         "descent_chop_cycle_share": float(
                             cnt[..., 6].astype(np.float64).sum()
-                            / max(1.0, cnt[..., 6:8].astype(np.float64).sum()))}
+                            / max(1.0, cnt[..., 6:8].astype(np.float64).sum())),
+                        "histograms": {k: log2_histogram(cnt[..., i])
+                                       for k, i in (("sweeps", 0), ("chop_probes", 1),
+                                                    ("polish_pivots", 2))}}
 
     # the same fits under option variants that the exact finish makes
     # result-neutral (the four-section chop; chop = 0: the polish straight

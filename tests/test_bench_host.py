@@ -61,3 +61,12 @@ def test_row_updates_count():
     # (sweeps * p + pivots) * n per fit
     want = (4 * 3 + 0) * 10 + (2 * 3 + 7) * 10 + (1 * 5 + 5) * 20 + (3 * 5 + 0) * 20
     assert b.row_updates(batch, cnt, 2) == want
+
+
+def test_log2_histogram():
+    b = _bench()
+    h = b.log2_histogram(np.array([0, 1, 2, 3, 4, 7, 8, 15, 16, 1000]))
+    assert h["lower_edges"] == [0, 1, 2, 4, 8, 16, 32, 64, 128, 256, 512]
+    assert h["counts"] == [1, 1, 2, 2, 2, 1, 0, 0, 0, 0, 1]
+    assert sum(h["counts"]) == 10
+    assert b.log2_histogram(np.zeros(3, np.int32)) == {"lower_edges": [0], "counts": [3]}
