@@ -330,6 +330,37 @@ def test_optimum_along_lambda_is_nondecreasing_and_concave():
     assert np.all(slopes <= l1[:-1] + 1e-9) and np.all(slopes >= l1[1:] - 1e-9)
 
 
+def test_non_unique_optima_are_flagged():
+    # a duplicated column: only b_0 + b_1 matters to the residual and, with
+    # equal signs, to the penalty, so every such split of the optimum is
+    # optimal (brute force finds several optimal vertices).  The method must
+    # flag it NONUNIQUE and the certificate must deny uniqueness, both at the
+    # vertex returned and at the midpoint of two optimal vertices (an optimal
+    # point that is no vertex: fewer zero residuals than nonzero coefficients)
+    rng = np.random.default_rng(31)
+    n = 30
+    x, z = rng.standard_normal(n), rng.standard_normal(n)
+    X = np.column_stack([x, x, z])
+    y = 2.0 * x - z + rng.laplace(0, 0.3, n)
+    lam = 0.1 * oracle.lambda_max(X, y)
+    fb, bb, nd = oracle.brute_force(X, y, lam)
+    assert nd > 1
+    r = oracle.fit_path(X, y, [lam])
+    assert rel(r["f"][0], fb) < 1e-11
+    assert r["status"][0] & oracle.FIT_NONUNIQUE
+    gap, info = oracle.certify(X, y, r["b"][0], lam)
+    assert gap < 1e-9 and not info["unique"]
+    s01 = r["b"][0][0] + r["b"][0][1]
+    mid = np.array([s01 / 2, s01 / 2, r["b"][0][2]])
+    assert rel(F(X, y, mid, lam), fb) < 1e-11  # the optimal set is convex
+    gap, info = oracle.certify(X, y, mid, lam)
+    assert gap < 1e-9 and not info["unique"]
+    # without the duplicate the optimum is a strict vertex and is not flagged
+    ru = oracle.fit_path(X[:, [0, 2]], y, [lam])
+    assert ru["status"][0] == oracle.FIT_OK
+    assert oracle.certify(X[:, [0, 2]], y, ru["b"][0], lam)[1]["unique"]
+
+
 # ---------------------------------------------------------------- certificate
 
 def test_certificate_detects_suboptimal_points():

@@ -75,6 +75,8 @@ MUTANTS = {
         "bp[m].z = r[i] / vi;", "bp[m].z = -r[i] / vi;"),
     "polish: coordinate breakpoint sign": (
         "bp[m].z = -b[j] / d[j];", "bp[m].z = b[j] / d[j];"),
+    "polish: non-unique optima never flagged": (
+        "*nonunique = phantoms > 0 || at_cap > 0;", "*nonunique = 0;"),
     # lambda_max
     "lambda_max: y instead of sign(y)": (
         "c += X[(size_t)i * p + j] * sgn(y[i]);", "c += X[(size_t)i * p + j] * y[i];"),
@@ -93,6 +95,8 @@ MUTANTS = {
     "certificate: dual signs flipped": (
         "if (fabs(r[i]) > eps_r * fmax(1.0, ymax)) u[i] = sgn(r[i]);",
         "if (fabs(r[i]) > eps_r * fmax(1.0, ymax)) u[i] = -sgn(r[i]);"),
+    "certificate: uniqueness without |E| = |S|": (
+        "int solved = 1, unique_ok = (ne == ns);", "int solved = 1, unique_ok = 1;"),
     "certificate: no scaling into the lambda box": (
         "if (lam > 0) theta = fmax(theta, cmax / lam);", "if (lam > 0 && 0) theta = fmax(theta, cmax / lam);"),
     # active-set gradient
@@ -118,6 +122,7 @@ PINS = [
     ("test_sign_symmetries_and_a_zero_column", ()),
     ("test_optimum_along_lambda_is_nondecreasing_and_concave", ()),
     ("test_bad_lambda_status", ()),
+    ("test_non_unique_optima_are_flagged", ()),
     ("test_tiny_golden_brute_simplex_method_agree", ()),
 ] + [("test_random_tiny_brute_equals_simplex_equals_method", (s,)) for s in range(6)] + [
     ("test_chop_is_exact_on_two_coordinates", (3,)),
