@@ -395,14 +395,19 @@ def test_plain_ccd_stalls_but_method_does_not():
 
 
 def test_chop_only_variant_is_not_always_optimal_but_never_worse():
+    # without the polish the method ends with coordinate descent after the
+    # chop (Sections 3.3-3.5): its point is never worse than plain CCD's and
+    # is itself an axis-wise minimum of F, so descent from it does not move
     rng = np.random.default_rng(43)
-    for trial in range(4):
+    for trial in range(8):
         X, y = rand_problem(rng, 60, 6)
         lam = 0.05 * oracle.lambda_max(X, y)
         bc, _ = oracle.ccd(X, y, lam)
         o = oracle.default_opts(polish=0)
         r = oracle.fit_path(X, y, [lam], opts=o)
         assert r["f"][0] <= F(X, y, bc, lam) * (1 + 1e-12)
+        again, _ = oracle.ccd(X, y, lam, b0=r["b"][0])
+        np.testing.assert_allclose(again, r["b"][0], atol=1e-9)
 
 
 @pytest.mark.parametrize("sections", [3, 4])

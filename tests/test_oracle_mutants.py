@@ -106,6 +106,25 @@ MUTANTS = {
     "gradient: X_RS instead of its transpose": (
         "M[(size_t)a * ns + c] = X[(size_t)R[c] * p + S[a]];",
         "M[(size_t)a * ns + c] = X[(size_t)R[a] * p + S[c]];"),
+    "gradient: validation target term sign": (
+        "gyv[v] = up * s;", "gyv[v] = -up * s;"),
+    "gradient: training design rows term sign": (
+        "gX[(size_t)R[c] * p + S[a]] = -up * gS[c] * b[S[a]];",
+        "gX[(size_t)R[c] * p + S[a]] = up * gS[c] * b[S[a]];"),
+    "gradient: nonzero lambda derivative": (
+        "  *glam = 0.0;\n  double* gS", "  *glam = 1.0;\n  double* gS"),
+    "lambda_max: no absolute value": (
+        "best = fmax(best, fabs(c));", "best = fmax(best, c);"),
+    "weighted median: flat segment's upper end returns the lower": (
+        "if (cur >= hi) { *owner = bp[g].id; return hi; }",
+        "if (cur >= hi) { *owner = bp[g].id; return lo; }"),
+    "chop: never run at p = 2": (
+        "if (!is_opt && o->chop && p >= 2) {", "if (!is_opt && o->chop && p >= 3) {"),
+    "chop: probe does not fix b_k": (
+        "    c->b[k] = t;\n  }", "  }"),
+    "chop: stale residual after an improving chop": (
+        "    memcpy(b, bb, sizeof(double) * p);\n    residual(n, p, X, y, b, r);",
+        "    memcpy(b, bb, sizeof(double) * p);"),
     "gradient: validation design term sign": (
         "gXv[(size_t)v * p + j] = -up * s * b[j];", "gXv[(size_t)v * p + j] = up * s * b[j];"),
 }
