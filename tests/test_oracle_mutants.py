@@ -75,6 +75,11 @@ MUTANTS = {
         "bp[m].z = r[i] / vi;", "bp[m].z = -r[i] / vi;"),
     "polish: coordinate breakpoint sign": (
         "bp[m].z = -b[j] / d[j];", "bp[m].z = b[j] / d[j];"),
+    "polish: the released hyperplane stays in the basis": (
+        "basis[q].code = own;", "basis[q].code = basis[q].code;"),
+    "polish: zero coordinates snapped to 1": (
+        "if (basis[k].code < 0 && !basis[k].phantom) b[-basis[k].code - 1] = 0.0;",
+        "if (basis[k].code < 0 && !basis[k].phantom) b[-basis[k].code - 1] = 1.0;"),
     "polish: non-unique optima never flagged": (
         "*nonunique = phantoms > 0 || at_cap > 0;", "*nonunique = 0;"),
     # lambda_max
@@ -91,6 +96,17 @@ MUTANTS = {
     "simplex: negative part added": (
         "else if (bas[i] < 2 * p) b_out[bas[i] - p] -= xv;",
         "else if (bas[i] < 2 * p) b_out[bas[i] - p] += xv;"),
+    "simplex: ratio test on negative entries": (
+        "if (a > eps) {\n        double ratio", "if (a < -eps) {\n        double ratio"),
+    "simplex: enters a positive reduced cost": (
+        "for (int j = 0; j < m; ++j) if (z[j] < -eps) { e = j; break; }",
+        "for (int j = 0; j < m; ++j) if (z[j] > eps) { e = j; break; }"),
+    "simplex: pivot row not normalised": (
+        "for (int j = 0; j <= m; ++j) pr[j] /= pv;", ""),
+    "gauss_solve: right-hand side not eliminated": (
+        "      rhs[i] -= l * rhs[k];\n", ""),
+    "brute force: keeps the last minimiser, not the first": (
+        "      if (f < fbest - tolf) {", "      if (f <= fbest + tolf) {"),
     # duality-gap certificate
     "certificate: dual signs flipped": (
         "if (fabs(r[i]) > eps_r * fmax(1.0, ymax)) u[i] = sgn(r[i]);",
