@@ -21,7 +21,7 @@ Parity status of each function (what pins it in tests/test_oracle.py):
   grad            central finite differences of refits at generic points
                   (training y and X rows), of the loss itself (validation
                   y and X rows); exact scaling by the upstream factor
-Each of 47 planted mistakes in the C source fails at least one of these
+Each of 51 planted mistakes in the C source fails at least one of these
 pins (tests/test_oracle_mutants.py).
 """
 from __future__ import annotations

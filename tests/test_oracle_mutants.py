@@ -47,6 +47,16 @@ MUTANTS = {
         "work[m].w = fabs(x);", "work[m].w = x * x;"),
     "axis update: doubled penalty weight": (
         "work[m].w = lam; work[m].id = COORD_ID(j);", "work[m].w = 2.0 * lam; work[m].id = COORD_ID(j);"),
+    "axis update: b_j not updated with the residual": (
+        "    for (int i = 0; i < n; ++i) r[i] -= X[(size_t)i * p + j] * d;\n    b[j] = t;",
+        "    for (int i = 0; i < n; ++i) r[i] -= X[(size_t)i * p + j] * d;"),
+    "ccd: convergence measured on the last move only": (
+        "mx = fmax(mx, fabs(d));", "mx = fabs(d);"),
+    "chop: probe objective without the absolute value": (
+        "for (int i = 0; i < n; ++i) f += fabs(r[i]);\n  for (int j = 0; j < p; ++j) f += lam * fabs(b[j]);\n  return f;\n}\n\n/* ---",
+        "for (int i = 0; i < n; ++i) f += r[i];\n  for (int j = 0; j < p; ++j) f += lam * fabs(b[j]);\n  return f;\n}\n\n/* ---"),
+    "polish: gradient includes the basis rows": (
+        "      if (inb[i]) continue;\n      double s = sgn(r[i]);", "      double s = sgn(r[i]);"),
     "axis update: residual update sign": (
         "for (int i = 0; i < n; ++i) r[i] -= X[(size_t)i * p + j] * d;\n    b[j] = t;",
         "for (int i = 0; i < n; ++i) r[i] += X[(size_t)i * p + j] * d;\n    b[j] = t;"),
