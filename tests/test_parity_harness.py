@@ -85,3 +85,40 @@ def test_parallel_form_reports_the_same(case):
     par = compare_parallel(batch, lam, bb, obj, st, range(6), workers=3)
     assert par["checked"] == one["checked"]
     assert sorted(map(str, par["bad"])) == sorted(map(str, one["bad"]))
+
+
+def test_gradient_check_accepts_the_oracle_and_rejects_planted_errors():
+    from test_gpu_backward import _check_against_oracle
+    d = synth.diff(B=6, n=140, n_train=110, p=6, seed=3)
+    tr, va = d["train"], d["val"]
+    B, P = 6, 6
+    lam = np.array([0.1 * oracle.lambda_max(*oracle.problem(tr, q)) for q in range(B)], np.float32)
+    up = np.linspace(0.5, 2.0, B)
+    g = dict(y=np.zeros(len(tr["y"])), X=np.zeros((len(tr["y"]), P)), yv=np.zeros(len(va["y"])),
+             Xv=np.zeros((len(va["y"]), P)), lam=np.zeros(B), status=np.zeros(B, np.int32),
+             loss=np.zeros(B))
+    bg = np.zeros((B, P), np.float32)
+    for q in range(B):
+        X, y = oracle.problem(tr, q)
+        Xv, yv = oracle.problem(va, q)
+        r = oracle.fit_path(X, y, [float(lam[q])])
+        bg[q] = r["b"][0]
+        og = oracle.grad(X, y, r["b"][0], r["basis"][0], Xv, yv, up=float(up[q]))
+        o0, o1 = tr["offsets"][q], tr["offsets"][q + 1]
+        v0, v1 = va["offsets"][q], va["offsets"][q + 1]
+        g["y"][o0:o1], g["X"][o0:o1] = og["gy"], og["gX"]
+        g["yv"][v0:v1], g["Xv"][v0:v1] = og["gyv"], og["gXv"]
+        g["loss"][q] = np.abs(yv - Xv @ r["b"][0]).sum()
+        g["status"][q] = 0 if og["ok"] else 4
+    assert _check_against_oracle(g, bg, lam, up, tr, va, range(B)) >= B // 2
+    for key, idx, delta in [("y", None, 0.1), ("Xv", None, 0.1), ("loss", 0, 1.0), ("lam", 0, 0.5)]:
+        bad = {k: v.copy() for k, v in g.items()}
+        if idx is None:  # a gradient entry of a checked problem's rows
+            o0 = tr["offsets"][0] if key == "y" else va["offsets"][0]
+            nz = np.flatnonzero(np.atleast_2d(bad[key].T)[0][o0:] != 0)
+            pos = o0 + (nz[0] if len(nz) else 0)
+            bad[key][pos] += delta
+        else:
+            bad[key][idx] += delta
+        with pytest.raises(AssertionError):
+            _check_against_oracle(bad, bg, lam, up, tr, va, range(B))
