@@ -122,3 +122,23 @@ def test_gradient_check_accepts_the_oracle_and_rejects_planted_errors():
             bad[key][idx] += delta
         with pytest.raises(AssertionError):
             _check_against_oracle(bad, bg, lam, up, tr, va, range(B))
+
+
+def test_vertex_from_basis_codes_reproduces_the_oracle():
+    # the large-workload test rebuilds the FP64 vertex of a reported basis
+    # (row codes i >= 0, coordinate codes -(j+1)); on the oracle's own basis
+    # it must give the oracle's vertex
+    from test_gpu_large import _vertex
+    rng = np.random.default_rng(5)
+    checked = 0
+    for n, p in [(40, 3), (120, 8)]:
+        X = rng.standard_normal((n, p))
+        y = X @ np.where(rng.random(p) < 0.5, rng.uniform(-2, 2, p), 0.0) + rng.laplace(0, 0.5, n)
+        for frac in (0.5, 0.05):
+            lam = frac * oracle.lambda_max(X, y)
+            r = oracle.fit_path(X, y, [lam])
+            if r["status"][0] != oracle.FIT_OK:
+                continue
+            np.testing.assert_allclose(_vertex(X, y, r["basis"][0]), r["b"][0], atol=1e-9)
+            checked += 1
+    assert checked >= 2
