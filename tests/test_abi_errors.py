@@ -267,3 +267,20 @@ def test_empty_problem_sets_return_ok_without_work(lib):
     assert lib.ladlasso_path_loss(*args[:4], C.byref(h.d), h.b.ctypes.data, out.ctypes.data,
                                   None) == ll.OK
     assert _backward(lib, h) == ll.OK
+
+
+def test_workspace_size_is_aligned_and_monotone(lib):
+    f = lib.ladlasso_workspace_size
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        B = int(rng.integers(0, 5000))
+        P = int(rng.integers(1, KMAXP + 1))
+        rows = int(rng.integers(0, 10 ** 7))
+        L = int(rng.integers(1, 64))
+        w = f(B, P, rows, L)
+        assert w > 0 and w % 256 == 0, (B, P, rows, L, w)
+        assert f(B + 1, P, rows, L) >= w
+        assert f(B, P, rows + 1000, L) > w
+        if P + 4 <= KMAXP:
+            assert f(B, P + 4, rows, L) >= w
+        assert f(B, P, rows, L + 1) == w  # the path length does not change it
