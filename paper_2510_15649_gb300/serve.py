@@ -248,6 +248,13 @@ def serve_pools(pools: list, trace: list, time_scale: float, budget: int) -> tup
                     pl._admit(reqs, rids)
         n_active = sum(len(pl._active()) for pl in pools)
         if n_active == 0:
+            if queue:
+                # nothing runs, so every slot and the whole budget are free and
+                # the head request (which fits a class and the budget) would
+                # have been admitted: the bookkeeping is broken, and waiting
+                # would never end
+                raise RuntimeError("serving stalled: requests wait, nothing runs and "
+                                   "none can be admitted")
             if nxt < len(trace):  # idle until the next arrival
                 time.sleep(max(0.0, min(arrive[nxt] - time.perf_counter(), 1e-3)))
             continue

@@ -82,6 +82,8 @@ class FakeLibrary:
         nr, p = pr.n_rows.numpy(), pr.p.numpy()
         active = np.nonzero(np.isfinite(lam))[0]
         assert np.all(nr[active] > 0), "a slot with a lambda holds no rows"
+        # the server's contract: idle slots are passed with NaN and 0 rows
+        assert np.all(nr[~np.isfinite(lam)] == 0), "an idle slot still passes rows"
         self.max_used = max(self.max_used, int((nr[active] * p[active]).sum()))
         b0 = b_init.numpy()[:, 0].copy()
         b, obj, st = out["b"].numpy(), out["obj"].numpy(), out["status"].numpy()
@@ -262,3 +264,14 @@ def test_slot_classes_refuse_a_request_no_class_holds(fake):
         ClassedServer([(2, 100, 8), (2, 300, 8)], L=2, device="cpu").run([big])
     with pytest.raises(ValueError):
         ClassedServer([], device="cpu")
+
+
+def test_broken_bookkeeping_raises_instead_of_waiting_forever(fake):
+    # a server whose free-slot list was lost can admit nothing while nothing
+    # runs: it must report that, not spin
+    from paper_2510_15649_gb300.serve import Server
+    fake()
+    srv = Server(slots=2, cap=300, P=8, L=2, device="cpu")
+    srv.free = []
+    with pytest.raises(RuntimeError, match="stalled"):
+        srv.run(_trace(n=2), time_scale=0.0)
