@@ -39,7 +39,8 @@ def _broken(**kw):
 
 
 @pytest.mark.parametrize("case", [
-    "X float64", "X transposed", "X narrower than P", "X 1-D", "y float64", "y 2-D",
+    "X float64", "X transposed", "X every other column", "X narrower than P", "X 1-D",
+    "y float64", "y 2-D",
     "y strided", "offsets int32", "offsets empty", "row_idx int64", "row_idx short",
     "p wrong count", "p int64", "n_rows float", "y on another device"])
 def test_layout_errors(case):
@@ -48,6 +49,8 @@ def test_layout_errors(case):
     bad = {
         "X float64": dict(X=X.double()),
         "X transposed": dict(X=X.t().contiguous().t()),
+        # rows far enough apart, but the columns are not adjacent
+        "X every other column": dict(X=torch.zeros((X.shape[0], 2 * X.shape[1]))[:, ::2]),
         "X narrower than P": dict(X=X[:, :4].contiguous()),
         "X 1-D": dict(X=X.reshape(-1)),
         "y float64": dict(y=y.double()),
