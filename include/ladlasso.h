@@ -250,7 +250,11 @@ int ladlasso_fit_batched_thread(const float* X, const float* y, const int32_t* r
  *   grad_Xv [total validation rows x P_cols].
  * A problem whose vertex is not strict gets NaN gradients and status bit
  * LADLASSO_FIT_NONUNIQUE in grad_status [B] (may be NULL).  val_loss [B]
- * (may be NULL) receives the validation loss itself. */
+ * (may be NULL) receives the validation loss itself.
+ * Host-checkable errors, before any launch: the problem-set checks of
+ * ladlasso_fit_batched; LADLASSO_ERR_INVALID for pos outside 0..L-1, a NULL
+ * b_out, basis_out, voffsets, grad_up or gradient output, ldXv < P_cols,
+ * total_vrows < 0, or validation rows without Xv or yv. */
 int ladlasso_fit_backward(const float* X, const float* y, const int32_t* row_idx,
                           const int64_t* offsets, const ladlasso_dims* dims, int32_t pos,
                           const float* b_out, const int32_t* basis_out,
