@@ -208,7 +208,10 @@ int ladlasso_fit_batched(const float* X, const float* y, const int32_t* row_idx,
  * row_idx, offsets and dims describe the held-out rows like a problem set
  * (dims: B, P_cols, L, ldX, rows_X, total_rows, p; other fields unused; no
  * workspace).  A problem with out-of-range rows, bad offsets or a
- * non-finite residual gets NaN.  loss_out [B*L] device. */
+ * non-finite residual gets NaN.  loss_out [B*L] device.
+ * LADLASSO_ERR_INVALID, before any launch, for a NULL dims, offsets, b_out
+ * or loss_out, B < 0, L < 1, P_cols outside 1..256, ldX < P_cols, missing
+ * X or y for a nonempty set, or more slots than X rows without row_idx. */
 int ladlasso_path_loss(const float* X, const float* y, const int32_t* row_idx,
                        const int64_t* offsets, const ladlasso_dims* dims, const float* b_out,
                        float* loss_out, ladlasso_stream_t stream);
