@@ -14,6 +14,12 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
+    # a hang (a bug in a loop, a stuck child process) fails its test after
+    # 20 minutes instead of stalling the run, where pytest-timeout is present
+    if config.pluginmanager.hasplugin("timeout"):
+        for it in items:
+            if it.get_closest_marker("timeout") is None:
+                it.add_marker(pytest.mark.timeout(1200))
     try:
         import torch
         has_gpu = torch.cuda.is_available()
