@@ -12,10 +12,8 @@ instead (bounded samples of the same workload on the host cores).
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -184,40 +182,28 @@ def batch_rows(batch, q):
 
 
 def row_updates(batch, counters, B):
-    """Row-updates (one row's part in one 1-D weighted-median step) per fit:
-    CCD/probe sweeps x p x n + polish steps x n (approximate: restricted
-    sweeps skip one axis)."""
+    """Row-updates per launch: one row's part in one 1-D weighted-median
+    step (an axis step, a chop probe's axis step or a polish edge search),
+    i.e. n x the fit's 1-D steps (counter slot 5), summed over fits."""
     n = np.diff(batch["offsets"])[:B].astype(np.float64)
-    p = batch["p"][:B].astype(np.float64)
-    sw = counters[:, :, 0].astype(np.float64)
-    pv = counters[:, :, 2].astype(np.float64)
-    return float(np.sum((sw * p[:, None] + pv) * n[:, None]))
+    sel = counters[:, :, 5].astype(np.float64)
+    return float(np.sum(sel * n[:, None]))
+
+
+def smem_bytes(batch, counters, B):
+    """Algorithmic shared-memory bytes per launch of the one-warp fit kernel:
+    every selection pass reads each row's column element and residual (8 B
+    a row; counter slot 4 counts passes) and every 1-D step ends with the
+    residual update, which reads both and writes the residual (12 B a row;
+    slot 5 counts steps).  20 B per row-update when a step takes one pass."""
+    n = np.diff(batch["offsets"])[:B].astype(np.float64)
+    passes = counters[:, :, 4].astype(np.float64)
+    sel = counters[:, :, 5].astype(np.float64)
+    return float(np.sum((8.0 * passes + 12.0 * sel) * n[:, None]))
 
 
 def log(*a):
     print("[bench]", *a, file=sys.stderr, flush=True)
-
-
-def profile_traffic(name: str, source: str, launch_tag: str | None):
-    """DRAM bytes per launch recorded in profiles/<name> by an ncu capture
-    (lines `traffic_bytes_per_launch[<shape>]: <bytes>`), if it was taken on
-    the current code of the kernel (the SHA-256 of its source without
-    comments is recorded beside the numbers) with the same launch shape;
-    None otherwise."""
-    try:
-        text = open(os.path.join(ROOT, "profiles", name)).read()
-        # the code of the kernel source: `//` comments, trailing blanks and
-        # empty lines removed, so comment edits keep a capture valid
-        code = [re.sub(r"//.*$", "", ln).rstrip()
-                for ln in open(os.path.join(ROOT, source)).read().split("\n")]
-        cur = hashlib.sha256("\n".join(ln for ln in code if ln.strip()).encode()).hexdigest()
-    except OSError:
-        return None
-    h = re.search(r"kernel_code_sha256:\s*([0-9a-f]{64})", text)
-    if not h or h.group(1) != cur or launch_tag is None:
-        return None
-    m = re.search(r"traffic_bytes_per_launch\[" + re.escape(launch_tag) + r"\]:\s*([0-9.eE+]+)", text)
-    return float(m.group(1)) if m else None
 
 
 def main():
@@ -402,7 +388,6 @@ def main():
     # parity on a sample of fits against the FP64 oracle
     if rank == 0 and args.parity_sample > 0:
         import oracle
-        sys.path.insert(0, os.path.join(ROOT, "tests"))
         oracle.build()
         bh = out["b"].cpu().numpy()
         lh = lam.cpu().numpy()
@@ -421,29 +406,29 @@ def main():
         line["parity_sample"] = {"problems": qs, "fits": len(qs) * L, "worst_rel_obj": worst,
                                  "fails": int(fails)}
 
-    # roofline of the fit kernel: 6 flops per row-update against the FP32 FMA peak
+    # roofline of the fit kernel: shared-memory bandwidth, the bound for
+    # designs held in shared memory.  Algorithmic bytes from the kernel's own
+    # pass and step counters (smem_bytes) against 32 banks x 4 B per clock
+    # per SM at the sampled clock; the ALU view (6 flops per row-update
+    # against the FP32 FMA peak) is reported beside it
     ru = row_updates(batch, cnt, B)
+    sb = smem_bytes(batch, cnt, B)
     clk_s = clk.summary()
     mhz = clk_s.get("sm_mhz") or 1900.0
-    flops_per_ru = 6.0  # key (div+add), weight accumulate/compare, residual FMA
-    achieved = flops_per_ru * ru / t_fit / 1e12
-    peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x clock
-    line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak,
-                        "traffic": profile_traffic(
-                            "launches_batched4096.md", "paper_2510_15649_gb300/csrc/fit_block.cu",
-                            None if launch is None else
-                            f"{launch.group_threads}x{launch.fits_per_block}/o{launch.work_order}"),
-                        "kernel": "fit_block_kernel", "kernel_ms": 1e3 * t_fit,
-                        "row_updates_per_launch": ru}
-    # the same kernel against shared-memory bandwidth: 12 algorithmic bytes
-    # per row-update (column element and residual read, residual write)
-    # against 32 banks x 4 B per clock per SM
     smem_peak = 152 * 32 * 4 * mhz * 1e6 / 1e9
-    smem_ach = 12.0 * ru / t_fit / 1e9
-    line["roofline_smem"] = {"bound": "smem", "achieved": smem_ach, "peak": smem_peak,
-                             "unit": "GB/s", "frac": smem_ach / smem_peak,
-                             "bytes_per_row_update": 12, "kernel": "fit_block_kernel"}
+    smem_ach = sb / t_fit / 1e9
+    line["roofline"] = {"bound": "smem", "achieved": smem_ach, "peak": smem_peak,
+                        "unit": "GB/s", "frac": smem_ach / smem_peak, "traffic": None,
+                        "peak_source": "152 SMs x 128 B/clock x sampled SM clock",
+                        "kernel": "fit_block_kernel", "kernel_ms": 1e3 * t_fit,
+                        "bytes_per_launch": sb, "row_updates_per_launch": ru,
+                        "bytes_per_row_update": sb / max(1.0, ru)}
+    flops_per_ru = 6.0  # key (div+add), weight accumulate/compare, residual FMA
+    alu_ach = flops_per_ru * ru / t_fit / 1e12
+    alu_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x clock
+    line["roofline_alu"] = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak,
+                            "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
+                            "flops_per_row_update": flops_per_ru, "kernel": "fit_block_kernel"}
     line["clocks"] = clk_s
     # per-fit counters of the last timed step (work the method did)
     def pct(a):
@@ -693,6 +678,17 @@ def main():
                                 "kind": "oracle",
                                 "sample": f"problems 0..{done - 1} x {L} lambdas of the workload "
                                           f"({dt:.1f} s, chunks of {chunk} problems)"}
+        # the same oracle on one core: problems in order, one at a time,
+        # until at least 5 s of CPU work has been timed
+        done1, dt1 = 0, 0.0
+        while done1 < B and dt1 < 5.0:
+            t0 = time.perf_counter()
+            oracle.fit_batch(batch, lh, problems=np.arange(done1, done1 + 1), nthreads=1)
+            dt1 += time.perf_counter() - t0
+            done1 += 1
+        line["cpu_baseline"]["one_core"] = {
+            "value": done1 * L / dt1, "unit": "fits/s", "cores": 1,
+            "sample": f"problems 0..{done1 - 1} x {L} lambdas of the workload ({dt1:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

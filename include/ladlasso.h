@@ -282,6 +282,8 @@ int ladlasso_fit_backward(const float* X, const float* y, const int32_t* row_idx
  * LADLASSO_ERR_NOMEM before any launch.
  * The first call on a device looks up the array's device address (with
  * that device current); make that first call before any stream capture.
+ * First calls from several host threads at once are safe: each looks the
+ * address up and records the same value.
  * All calls on a device share the array and it keeps the last call's
  * contents: each call clears its control words itself, and calls whose
  * kernels overlap on the GPU (e.g. on two streams) race on the array --

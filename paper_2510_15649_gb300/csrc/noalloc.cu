@@ -8,6 +8,8 @@
 // or code whose memory budget is fixed at start-up.  They still own their
 // inputs and outputs; only the library's scratch (control words and the
 // gathered designs) comes from the array below.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace ll {
@@ -33,19 +35,23 @@ namespace {
 constexpr size_t kScratchBytes = (size_t)32 << 20;  // 32 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Per-device address of g_noalloc_scratch, found once with that device current.
+// Per-device address of g_noalloc_scratch, found once with that device
+// current.  Atomic: host threads that make their first calls on one device
+// at the same time each look the address up and store the same value.
 constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::atomic<unsigned char*> g_scratch_ptr[kMaxDevices] = {};
 
 int scratch_for_current_device(unsigned char** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LADLASSO_ERR_CUDA;
-  if (!g_scratch_ptr[dev]) {
+  unsigned char* ptr = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!ptr) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LADLASSO_ERR_CUDA;
-    g_scratch_ptr[dev] = (unsigned char*)p;
+    ptr = (unsigned char*)p;
+    g_scratch_ptr[dev].store(ptr, std::memory_order_release);
   }
-  *out = g_scratch_ptr[dev];
+  *out = ptr;
   return LADLASSO_OK;
 }
 

@@ -1,6 +1,6 @@
 """Host helpers of bench.py: the clock summary that accepts or rejects a
-run, the rule that reports ncu traffic only for the kernel code and launch
-shape it was captured on, and the row-update count behind the roofline."""
+run, and the row-update and shared-memory byte counts behind the
+roofline."""
 import importlib.util
 import os
 
@@ -32,35 +32,24 @@ def test_clock_summary():
     assert cs.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
 
 
-def test_traffic_only_for_the_captured_code_and_shape():
-    b = _bench()
-    name = "launches_batched4096.md"
-    src = "paper_2510_15649_gb300/csrc/fit_block.cu"
-    text = open(os.path.join(ROOT, "profiles", name)).read()
-    assert "kernel_code_sha256:" in text and "traffic_bytes_per_launch[" in text
-    # another source file never matches the recorded code hash
-    assert b.profile_traffic(name, "paper_2510_15649_gb300/csrc/aux_kernels.cu", "32x3/o0") is None
-    # no launch shape, or one that was not captured
-    assert b.profile_traffic(name, src, None) is None
-    assert b.profile_traffic(name, src, "32x99/o1") is None
-    # a missing profile
-    assert b.profile_traffic("no_such_profile.md", src, "32x3/o0") is None
-    # a captured shape gives the recorded number, or None once the code has changed
-    v = b.profile_traffic(name, src, "32x3/o0")
-    assert v is None or (v > 0 and f"traffic_bytes_per_launch[32x3/o0]:" in text)
-
-
-def test_row_updates_count():
+def test_row_updates_and_smem_bytes():
     b = _bench()
     batch = dict(offsets=np.array([0, 10, 30], np.int64), p=np.array([3, 5], np.int32))
     cnt = np.zeros((2, 2, 8), np.int32)
-    cnt[0, :, 0] = [4, 2]   # sweeps of problem 0 at its two path positions
-    cnt[1, :, 0] = [1, 3]
-    cnt[0, :, 2] = [0, 7]   # polish pivots
-    cnt[1, :, 2] = [5, 0]
-    # (sweeps * p + pivots) * n per fit
-    want = (4 * 3 + 0) * 10 + (2 * 3 + 7) * 10 + (1 * 5 + 5) * 20 + (3 * 5 + 0) * 20
-    assert b.row_updates(batch, cnt, 2) == want
+    cnt[0, :, 4] = [6, 2]   # selection passes of problem 0 at its two path positions
+    cnt[1, :, 4] = [1, 9]
+    cnt[0, :, 5] = [4, 2]   # 1-D steps
+    cnt[1, :, 5] = [1, 7]
+    # n x steps per fit
+    assert b.row_updates(batch, cnt, 2) == (4 + 2) * 10 + (1 + 7) * 20
+    # n x (8 B per pass + 12 B per step) per fit
+    want = (8 * 6 + 12 * 4) * 10 + (8 * 2 + 12 * 2) * 10 + (8 * 1 + 12 * 1) * 20 + (8 * 9 + 12 * 7) * 20
+    assert b.smem_bytes(batch, cnt, 2) == want
+    # one pass per step: 20 B per row-update
+    one = np.zeros((1, 1, 8), np.int32)
+    one[0, 0, 4] = one[0, 0, 5] = 3
+    b1 = dict(offsets=np.array([0, 7], np.int64), p=np.array([2], np.int32))
+    assert b.smem_bytes(b1, one, 1) == 20 * b.row_updates(b1, one, 1)
 
 
 def test_log2_histogram():
