@@ -1858,6 +1858,26 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
   return it;
 }
 
+// Stall test (no pivots): is the descent point's vertex already optimal?
+// The test snaps b onto the vertex of the basis built from the hyperplanes
+// the axis steps landed on; an optimal vertex is kept, otherwise b and r
+// return to the descent point, where the method continues.
+template <int G>
+__device__ __noinline__ int stall_test(St& s, int* nonu) {
+  for (int c = gtid<G>(); c < s.p; c += G) s.bbest[c] = s.bv[c];
+  if (gwarp<G>() == 0) build_basis(s);
+  gsync<G>();
+  int is_opt = 0;
+  polish<G>(s, 0, &is_opt, nonu);
+  if (!is_opt) {
+    for (int c = gtid<G>(); c < s.p; c += G) s.bv[c] = s.bbest[c];
+    gsync<G>();
+    recompute_r<G>(s);
+    gsync<G>();
+  }
+  return is_opt;
+}
+
 // F at the vertex of the current basis (snap; +inf when singular).
 template <int G>
 __device__ __noinline__ float vertex_objective(St& s) {
@@ -2017,9 +2037,7 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
     if (sw < 0) status |= kFitMaxIters;
     int is_opt = 0, nonu = 0;
     long long t1 = clock64(); t_cd += t1 - t0; t0 = t1;
-    if (gwarp<G>() == 0) build_basis(s);
-    gsync<G>();
-    polish<G>(s, 0, &is_opt, &nonu);
+    is_opt = stall_test<G>(s, &nonu);
     if (is_opt) flags |= 1;
     t1 = clock64(); t_vx += t1 - t0; t0 = t1;
     if (!is_opt && A.o.chop && p >= 2) {
@@ -2034,9 +2052,7 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
       sw = ccd<G>(s, -1, A.o.max_sweeps);
       sweeps += sw < 0 ? -sw : sw;
       t1 = clock64(); t_cd += t1 - t0; t0 = t1;
-      if (gwarp<G>() == 0) build_basis(s);
-      gsync<G>();
-      polish<G>(s, 0, &is_opt, &nonu);
+      is_opt = stall_test<G>(s, &nonu);
       if (is_opt) flags |= 4;
     }
     if (!is_opt && A.o.polish) {

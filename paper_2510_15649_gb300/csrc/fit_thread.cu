@@ -383,6 +383,20 @@ struct TFit {
     recompute_r();
   }
 
+  // Stall test (no pivots): the vertex of the descent point's basis is kept
+  // when optimal; otherwise b and r return to the descent point.
+  __device__ int stall_test(int& nonu) {
+    for (int c = 0; c < p; ++c) bbest[c] = bv[c];
+    build_basis();
+    int is_opt = 0;
+    polish(0, is_opt, nonu);
+    if (!is_opt) {
+      for (int c = 0; c < p; ++c) bv[c] = bbest[c];
+      recompute_r();
+    }
+    return is_opt;
+  }
+
   // order-independent hash of the basis set
   __device__ unsigned basis_hash() const {
     unsigned h = 0u;
@@ -521,8 +535,7 @@ struct TFit {
       sweeps += s < 0 ? -s : s;
       if (s < 0) status |= kFitMaxIters;
       int is_opt = 0, nonu = 0;
-      build_basis();
-      polish(0, is_opt, nonu);
+      is_opt = stall_test(nonu);
       if (is_opt) flags |= 1;
       if (!is_opt && A.o.chop && p >= 2) {
         int kk = 0;
@@ -532,8 +545,7 @@ struct TFit {
         for (int c = 0; c < p; ++c) piv[c] = -2;
         s = ccd(-1, A.o.max_sweeps);
         sweeps += s < 0 ? -s : s;
-        build_basis();
-        polish(0, is_opt, nonu);
+        is_opt = stall_test(nonu);
         if (is_opt) flags |= 4;
       }
       if (!is_opt && A.o.polish) {

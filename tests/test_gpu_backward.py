@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import LAM_REL, MARGIN
+from gpu_common import well_separated
 from paper_2510_15649_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -69,15 +69,10 @@ def test_backward_full_size_sampled(ll):
 
 def _well_separated(X, y, ref, lam):
     """The parity bar's uniqueness test (tests/gpu_common.py): a strict
-    vertex with complementarity margin >= MARGIN whose support is the same
-    at lambda * (1 -+ LAM_REL), so float32 cannot land on another vertex."""
-    _, info = oracle.certify(X, y, ref["b"][0], lam)
-    if not info["unique"] or min(1.0 - info["u_e_max"], 1.0 - info["c_off_max"]) < MARGIN:
-        return False
-    sup = ref["b"][0] != 0
-    return all(np.array_equal(oracle.fit_path(X, y, [lam * (1.0 + sg * LAM_REL)],
-                                              b_init=ref["b"][0])["b"][0] != 0, sup)
-               for sg in (-1.0, 1.0))
+    vertex whose multipliers keep more slack than float32 can misjudge and
+    whose support is the same at lambda * (1 -+ LAM_REL), so float32 cannot
+    land on another vertex."""
+    return well_separated(X, y, ref["b"][0], ref["basis"][0], lam)
 
 
 def _check_against_oracle(g, bg, lam, upn, tr, va, qs, separated_only=False):

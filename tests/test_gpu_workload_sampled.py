@@ -54,3 +54,9 @@ def test_headline_workload_sampled_parity(ll):
     res = compare_parallel(batch, lam.cpu().numpy(), ref["b"], ref["obj"], ref["status"], qs)
     assert res["checked"] == len(qs) * L
     assert not res["bad"], res["bad"][:10]
+    # most sampled fits are unique at float32 resolution and so checked on
+    # support and coefficients, not on the objective alone (the oracle's own
+    # results qualify for 170 of these 192)
+    assert res["support_checked"] >= 0.75 * res["checked"], res
+    print(f"support-checked {res['support_checked']} of {res['checked']} fits, "
+          f"objective only {res['objective_only']}")

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import compare, compare_parallel
+from gpu_common import EXACT_CHOP_OPTS, compare, compare_parallel, exact_problems
 from paper_2510_15649_gb300 import synth
 
 L = 3
@@ -142,3 +142,23 @@ def test_vertex_from_basis_codes_reproduces_the_oracle():
             np.testing.assert_allclose(_vertex(X, y, r["basis"][0]), r["b"][0], atol=1e-9)
             checked += 1
     assert checked >= 2
+
+
+def test_exact_family_stays_exact_in_float32():
+    # premise of the GPU test that compares chop-only fits bit for bit: on
+    # these problems the oracle's results (and so every key, residual and
+    # objective on the way, which have no more bits) are dyadic rationals
+    # of at most 12 fractional bits below 2^8 in magnitude, objectives
+    # below 2^12: all exact in float32's 24-bit significand
+    probs, lam = exact_problems(73)
+    o = oracle.default_opts(tol_move=1e-6, **EXACT_CHOP_OPTS)
+    chopped = 0
+    for (Xq, yq), lq in zip(probs, lam[:, 0]):
+        X, y = Xq.astype(np.float64), yq.astype(np.float64)
+        r = oracle.fit_path(X, y, [float(lq)], opts=o)
+        b, f = r["b"][0], r["f"][0]
+        assert np.all(b * 4096 == np.round(b * 4096)) and np.abs(b).max() < 256
+        assert f * 4096 == round(f * 4096) and f < 4096
+        assert np.array_equal(X.astype(np.float32).astype(np.float64), X)
+        chopped += r["stats"][0]["chop_ran"]
+    assert chopped >= len(probs) // 2
