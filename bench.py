@@ -47,8 +47,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-thread", action="store_true", help="skip the thread-per-fit comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--serve-seconds", type=float, default=0.25,
-                    help="length of the Poisson arrival trace (20k requests/s)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the Poisson arrival trace")
+    ap.add_argument("--serve-rate", type=float, default=20000.0, help="requests/s offered")
+    ap.add_argument("--serve-light-rate", type=float, default=1000.0,
+                    help="requests/s of a second trace offered below capacity (0: none)")
+    ap.add_argument("--serve-light-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-classes", action="store_true",
+                    help="also serve the trace with slot classes (ClassedServer)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 20000 x 128 block-per-fit measurement")
     ap.add_argument("--large-problems", type=int, default=256)
@@ -63,6 +69,10 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="library's default launch shape")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch the step eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--shard", default="weak", choices=["weak", "cost"],
+                    help="N > 1: weak = a batch of --problems per rank (default); cost = one "
+                         "batch of --problems split across ranks in contiguous shares balanced "
+                         "by n*p*L (strong scaling)")
     ap.add_argument("--launch", default=None,
                     help="fixed launch shape GxF/oW (threads per fit, fits per block, work "
                          "order), e.g. 32x3/o0; skips the autotuner")
@@ -228,7 +238,15 @@ def main():
     from paper_2510_15649_gb300 import ladlasso as ll
 
     B, L = args.problems, args.L
-    batch = synth.batched(B=B, seed=1 + 1000 * rank)  # weak scaling: one batch per rank
+    shard = (0, B)
+    if args.shard == "cost":
+        # strong scaling: one batch, each rank fits a contiguous share whose
+        # cost (n * p * L per problem) is within one problem of 1/world
+        from paper_2510_15649_gb300.dist import cost_share
+        batch, shard = cost_share(synth.batched(B=B, seed=1), L, rank, world)
+        B = shard[1] - shard[0]
+    else:
+        batch = synth.batched(B=B, seed=1 + 1000 * rank)  # weak scaling: one batch per rank
     dev = torch.device("cuda", local)
     pr = ll.Problems.from_numpy(batch, device=dev)
     ws = ll.workspace(pr, L)
@@ -315,6 +333,11 @@ def main():
     from paper_2510_15649_gb300.dist import sum_over_ranks
     certified_all = sum_over_ranks(certified, dist, dev)  # the fits every rank certified
     value = certified_all / t_step
+    coverage_ok = None
+    if args.shard == "cost":
+        # the shares reassemble the batch: every problem fitted by exactly one rank
+        from paper_2510_15649_gb300.dist import covered_once
+        coverage_ok = covered_once(shard[0], shard[1], args.problems, dist, dev)
 
     # kernel-only time of the fit launch (events on the launching stream)
     lam_fixed = lam.clone()
@@ -368,9 +391,9 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "fits/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": workload(B, L), "problems_per_gpu": B, "lambdas": L,
+            "higher_is_better": True, "scaling": "strong" if args.shard == "cost" else "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload(args.problems, L), "problems_per_gpu": B, "lambdas": L,
                        "fits_per_gpu": fits, "l2": "flushed between timed steps (256 MB write)",
                        "step": graph_note,
                        "launch": None if launch is None else {
@@ -381,9 +404,12 @@ def main():
                                            round(1e3 * t, 2) for c, t in tuned.items()}}},
             "certified_fraction": certified / fits,
             "gpu_launches": launches_per_step * args.steps,
-            "problems_per_s": B * world / t_step,
+            "problems_per_s": (args.problems if args.shard == "cost" else B * world) / t_step,
             "e2e": {"value": certified_all / t_e2e, "unit": "fits/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}}
+    if args.shard == "cost":
+        line["config"].update(shard="cost", problems_total=args.problems,
+                              rank0_share=list(shard), coverage_ok=coverage_ok)
 
     # parity on a sample of fits against the FP64 oracle
     if rank == 0 and args.parity_sample > 0:
@@ -528,7 +554,10 @@ def main():
                 "roofline": {"bound": "hbm", "achieved": byts / tl / 1e9, "peak": hbm_peak,
                              "unit": "GB/s", "frac": byts / tl / 1e9 / hbm_peak,
                              "bytes_per_launch": byts, "traffic": None},
-                "pivots_mean": float(cb[..., 2].mean()), "passes_mean": float(cb[..., 4].mean())}
+                "pivots_mean": float(cb[..., 2].mean()), "passes_mean": float(cb[..., 4].mean()),
+                # share of the block's cycles in descent + chop (the rest is
+                # the stall tests and the polish: counter slots 6 and 7)
+                "descent_chop_cycle_share": float(cb[..., 6].sum() / max(1.0, cb[..., 6:8].sum()))}
             log(f"large {line['large']}")
             del pb, wsb, ob
             torch.cuda.empty_cache()
@@ -625,37 +654,96 @@ def main():
         except Exception as ex:  # report, do not fail the bench line
             line["cv"] = {"error": str(ex)}
 
-    # continuous-batching server on Poisson arrivals (20k requests/s)
+    # continuous-batching server on Poisson arrivals (20k requests/s for
+    # 10 s: the request designs are windows of one shared N(0,1) row bank,
+    # each request with its own coefficients, noise and outliers), then a
+    # second trace offered below capacity, where latency is service time
     if not args.no_serve and rank == 0:
+        from paper_2510_15649_gb300.serve import ClassedServer, Server
+        bank = 1 << 20
         try:
-            from paper_2510_15649_gb300.serve import Server
-            trace = synth.serve_trace(rate=20000.0, seconds=args.serve_seconds, seed=4)
-            srv = Server(slots=2048, cap=5000, P=64, L=8)
-            srv.run(trace[:64])  # warm-up on the first requests
-            srv = Server(slots=2048, cap=5000, P=64, L=8)
+            t0 = time.perf_counter()
+            trace = synth.serve_trace(rate=args.serve_rate, seconds=args.serve_seconds, seed=4,
+                                      bank_rows=bank)
+            log(f"serve trace {len(trace)} requests in {time.perf_counter() - t0:.1f}s")
+            # the trace's first 4096 requests as one problem set: the launch
+            # shape for this mix (5000-row slots hold only a few fits per SM,
+            # where several warps per fit pay) is autotuned on it, and the
+            # batched kernel's throughput on it is the serving arm's reference
+            mix = trace[:4096]
+            nn = np.array([r["X"].shape[0] for r in mix])
+            pp = np.array([r["X"].shape[1] for r in mix], np.int32)
+            off = np.concatenate([[0], np.cumsum(nn)]).astype(np.int64)
+            Xm = np.zeros((off[-1], 64), np.float32)
+            ym = np.zeros(off[-1], np.float32)
+            for k, r in enumerate(mix):
+                Xm[off[k]:off[k + 1], :pp[k]] = r["X"]
+                ym[off[k]:off[k + 1]] = r["y"]
+            pm = ll.Problems.from_numpy(dict(X=Xm, y=ym, row_idx=None, offsets=off, p=pp), device=dev)
+            pm.n_max = 5000  # the pool's slot capacity
+            wsm = ll.workspace(pm, 8)
+            lamm = ll.lambda_path(ll.lambda_max(pm, wsm), 8, 1e-3)
+            from paper_2510_15649_gb300 import tune
+            slaunch, stimes = tune.autotune(pm, lamm, sample_problems=512, repeats=1)
+            log(f"serve launch {slaunch}")
+            Server(slots=2048, cap=5000, P=64, L=8, launch=slaunch).run(trace[:256])  # warm-up
+            srv = Server(slots=2048, cap=5000, P=64, L=8, launch=slaunch)
             _, sst = srv.run(trace)
-            line["serve"] = dict(sst.summary(), workload=(
-                f"Poisson 20k req/s for {args.serve_seconds}s, n log-U[20,5000], "
-                "p log-U[2,64], L=8, 2048 slots"))
+            offered = len(trace) * 8 / args.serve_seconds
+            line["serve"] = dict(sst.summary(), offered_fits_per_s=offered, workload=(
+                f"Poisson {args.serve_rate:g} req/s for {args.serve_seconds:g}s, n log-U[20,5000], "
+                "p log-U[2,64], L=8, 2048 slots, several positions per launch for short requests"))
+            line["serve"]["launch"] = f"{slaunch.group_threads}x{slaunch.fits_per_block}/o{slaunch.work_order}"
             log(f"serve {line['serve']}")
+            del srv
+            # the batched kernel on the same request mix, one launch along
+            # the 8-point paths (the serving arm's throughput against this)
+            ll.fit(pm, lamm, ws=wsm, launch=slaunch)  # warm-up
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            om = ll.fit(pm, lamm, ws=wsm, launch=slaunch)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tm = e0.elapsed_time(e1) / 1e3
+            cm = int(np.sum((om["status"].cpu().numpy() & 3) == 0))
+            line["serve"]["batched_same_mix"] = {
+                "workload": "the trace's first 4096 requests as one batch, L=8, one launch",
+                "fits_per_s": cm / tm, "kernel_ms": 1e3 * tm,
+                "serving_share": line["serve"]["fits_per_s"] / (cm / tm)}
+            log(f"serve batched same mix {line['serve']['batched_same_mix']}")
+            del pm, wsm, om
         except Exception as ex:
             line["serve"] = {"error": str(ex)}
-        # the same trace and total slot count in slot classes sized to the
-        # request mix (58 % of requests have n <= 500, 83 % n <= 2000)
-        try:
-            from paper_2510_15649_gb300.serve import ClassedServer
-            classes = [(1280, 500, 64), (512, 2000, 64), (256, 5000, 64)]
-            ClassedServer(classes, L=8, device=dev).run(trace[:64])  # warm-up
-            csrv = ClassedServer(classes, L=8, device=dev)
-            _, cst = csrv.run(trace)
-            if isinstance(line.get("serve"), dict) and "error" not in line["serve"]:
+        if args.serve_light_rate > 0 and isinstance(line.get("serve"), dict):
+            try:
+                tl = synth.serve_trace(rate=args.serve_light_rate, seconds=args.serve_light_seconds,
+                                       seed=5, bank_rows=bank)
+                srv = Server(slots=2048, cap=5000, P=64, L=8, launch=slaunch)
+                _, lst = srv.run(tl)
+                line["serve"]["below_capacity"] = dict(
+                    lst.summary(), offered_fits_per_s=len(tl) * 8 / args.serve_light_seconds,
+                    workload=f"Poisson {args.serve_light_rate:g} req/s for "
+                             f"{args.serve_light_seconds:g}s, same request mix")
+                log(f"serve below capacity {line['serve']['below_capacity']}")
+                del srv
+            except Exception as ex:
+                line["serve"]["below_capacity"] = {"error": str(ex)}
+        if args.serve_classes and isinstance(line.get("serve"), dict):
+            # the same trace and total slot count in slot classes sized to the
+            # request mix (58 % of requests have n <= 500, 83 % n <= 2000)
+            try:
+                classes = [(1280, 500, 64), (512, 2000, 64), (256, 5000, 64)]
+                csrv = ClassedServer(classes, L=8, device=dev)
+                _, cst = csrv.run(trace)
                 line["serve"]["slot_classes"] = dict(
                     cst.summary(), classes="slots x rows (64 columns): 1280 x 500, 512 x 2000, "
                                            "256 x 5000")
-            log(f"serve slot classes {cst.summary()}")
-        except Exception as ex:
-            if isinstance(line.get("serve"), dict):
+                log(f"serve slot classes {cst.summary()}")
+            except Exception as ex:
                 line["serve"]["slot_classes"] = {"error": str(ex)}
+        torch.cuda.empty_cache()
 
     # CPU oracle baseline on a bounded sample
     if rank == 0 and not args.no_cpu_baseline:

@@ -128,18 +128,23 @@ void ladlasso_default_opts(ladlasso_opts* o);
  *            different streams, need workspaces of their own
  * opts     host pointer or NULL for defaults
  * group_threads   launch shape of ladlasso_fit_batched (and _noalloc):
- *            0 = automatic (one warp per fit up to 8192 rows, else one
- *            512-thread block per fit), 32 = one warp per fit, 512 = one
- *            block per fit; any other value is LADLASSO_ERR_INVALID.  The
+ *            threads per fit.  0 = automatic (one warp per fit up to 8192
+ *            rows, else one 512-thread block per fit); 32 = one warp per
+ *            fit; 64 or 128 = two or four warps per fit (each keeps the
+ *            current column in shared memory; the warps split the row
+ *            passes); 512 = one block per fit (columns read from global
+ *            memory); any other value is LADLASSO_ERR_INVALID.  The
  *            automatic choice also takes one block per fit when one warp's
  *            share of shared memory cannot hold n_max rows of P_cols columns
  *            but a block's can (from P_cols = 159 a warp holds fewer than
- *            8192 rows); ladlasso_launch_shape reports both limits.  The
- *            two shapes sum in different orders: results agree within the
+ *            8192 rows); ladlasso_launch_shape reports the limits.  The
+ *            shapes sum in different orders: results agree within the
  *            float32 tolerance, not bit for bit
- * fits_per_block  one-warp shape: at most this many fits per thread block
- *            (0 = as many as shared memory holds, at most 16); results do
- *            not depend on it.
+ * fits_per_block  shapes of up to 128 threads per fit: at most this many
+ *            fits per thread block (0 = as many as shared memory holds, at
+ *            most 512 threads a block, and no more than B / (SM count)
+ *            rounded up, so that a small problem set still spreads over
+ *            every SM); results do not depend on it.
  * work_order order in which the fits take problems: 0 = longest first
  *            (n * p), 1 = longest and shortest alternately (a smaller L2
  *            working set of resident designs); any other value is
@@ -218,7 +223,7 @@ int ladlasso_path_loss(const float* X, const float* y, const int32_t* row_idx,
 
 /* The launch shape ladlasso_fit_batched would use for `dims` (only
  * B-independent fields are read: P_cols, n_max, group_threads,
- * fits_per_block): threads per fit (32 or 512), fits per thread block, and
+ * fits_per_block): threads per fit (32, 64, 128 or 512), fits per thread block, and
  * the largest n_max that shape supports at this P_cols.  No launch, no
  * device access.  Returns LADLASSO_ERR_NOMEM when n_max exceeds max_rows,
  * LADLASSO_ERR_INVALID for invalid fields.  The paper has no counterpart:

@@ -96,7 +96,7 @@ struct St {
   float* vdg;        // block path: edge products x_i . d (global scratch)
   const FitArgs* a;
   const float* Xq;   // gathered design (column j at Xq + j*ld)
-  float* cb[2];      // one warp: double-buffered copy of the current column
+  float* cb[2];      // small groups: double-buffered copy of the current column
   int cur;           // buffer holding the column of the current axis step
   const float* yq;   // targets
   const float* colp; // per-row factor of the current 1-D problem: the column
@@ -108,10 +108,12 @@ struct St {
   // broadcast slots
   float lo, hi, acc, wpart, half, zstar, above;
   int part, m, owner, q, flag, iter, first, has_prev, bland;
+  int above_ok;   // s.above is the smallest key above the buffer (not a bound)
+  int need_next;  // an exact half needs the next key, which a pass must find
   int pexit;    // how the last polish ended (see polish)
   float worst;  // largest multiplier violation at the last test
   // fused-pass results
-  float p_wl, p_wi, p_wt, p_amin;
+  float p_wl, p_wi, p_wt;
   int p_cnt, p_ovf;
   // per-fit counters
   int passes, selects, sel_fail;
@@ -122,13 +124,24 @@ struct St {
 constexpr size_t kDynSmemLimit =
     227 * 1024 - ((16 * sizeof(St) + sizeof(FitArgs) + 256 + 1023) / 1024) * 1024;
 
-template <int G> __device__ __forceinline__ int gtid() { return G == 32 ? (threadIdx.x & 31) : threadIdx.x; }
-template <int G> __device__ __forceinline__ int gwarp() { return G == 32 ? 0 : (threadIdx.x >> 5); }
+template <int G> __device__ __forceinline__ int gtid() { return threadIdx.x & (G - 1); }
+template <int G> __device__ __forceinline__ int gwarp() { return G == 32 ? 0 : (gtid<G>() >> 5); }
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// Groups of up to 128 threads keep the current column in a shared-memory
+// double buffer; the block-per-fit group streams columns from global memory.
+template <int G> constexpr bool kSmemCols = G <= 128;
+
+// Barrier of one group: the warp itself, or the group's named barrier
+// (id 1 + group index; barrier 0 is the block's), which also orders the
+// group's shared- and global-memory accesses like __syncthreads.
 template <int G>
 __device__ __forceinline__ void gsync() {
-  if (G == 32) __syncwarp(); else __syncthreads();
+  if (G == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / G)), "n"(G) : "memory");
+  }
 }
 
 __device__ __forceinline__ float next_up(float v) { return v == -kInf ? v : nextafterf(v, kInf); }
@@ -155,7 +168,7 @@ __device__ __forceinline__ void reduce(St& s, float (&fs)[NS], float (&mn)[NM], 
   }
   if (W == 1) return;
   const int lane = lane_id(), warp = gwarp<G>();
-  __syncthreads();
+  gsync<G>();
   if (lane == 0) {
 #pragma unroll
     for (int e = 0; e < NS; ++e) s.redf[warp * 16 + e] = fs[e];
@@ -166,7 +179,7 @@ __device__ __forceinline__ void reduce(St& s, float (&fs)[NS], float (&mn)[NM], 
 #pragma unroll
     for (int e = 0; e < NJ; ++e) s.redi[warp * 16 + NI + e] = mi[e];
   }
-  __syncthreads();
+  gsync<G>();
 #pragma unroll
   for (int e = 0; e < NS; ++e) {
     float t = 0.f;
@@ -215,9 +228,9 @@ __device__ __forceinline__ int gscan(St& s, int cnt, int& total) {
   }
   int wtot = __shfl_sync(0xffffffffu, inc, 31);
   if (W == 1) { total = wtot; return inc - cnt; }
-  __syncthreads();
+  gsync<G>();
   if (lane == 0) s.redi[warp * 16 + 15] = wtot;
-  __syncthreads();
+  gsync<G>();
   int base = 0, tot = 0;
   for (int w = 0; w < W; ++w) {
     int c = s.redi[w * 16 + 15];
@@ -285,14 +298,25 @@ __device__ __noinline__ void bracket_from_samples(St& s, int ns, float frac) {
 // after it.  Exactly half: every t in [z, next] minimises; keep `cur`
 // inside, else take the nearer end (the far end gets no owner: the basis
 // builder then completes with coordinate hyperplanes).
+__device__ __forceinline__ void flat_rule(St& s, float z, float next, float cur) {
+  if (next < kInf) {
+    if (cur > z && cur < next) { s.zstar = cur; s.owner = kNone; }
+    else if (cur >= next) { s.zstar = next; s.owner = kNone; }
+  }
+}
+
+// `next` is the smallest buffered key above z (or the kept part's upper
+// bracket key); all keys outside the buffer above it are larger, so a
+// finite `next` is exact.  +inf is exact only when s.above is (no key
+// lies above the buffer); otherwise the caller's pass finds the key.
 __device__ __forceinline__ void finalize(St& s, float z, int owner, float cum, float next,
                                          float cur) {
   s.flag = 1;
   s.zstar = z;
   s.owner = owner;
-  if (cum == s.half && next < kInf) {
-    if (cur > z && cur < next) { s.zstar = cur; s.owner = kNone; }
-    else if (cur >= next) { s.zstar = next; s.owner = kNone; }
+  if (cum == s.half) {
+    if (next < kInf || s.above_ok) flat_rule(s, z, next, cur);
+    else s.need_next = 1;
   }
 }
 
@@ -311,12 +335,17 @@ __device__ __forceinline__ void decide(St& s, const float (&w5)[5], const float 
   while (g < 4 && !(s.half <= c[g])) ++g;
   while (g > 0 && !(w5[g] > 0.f)) --g;
   s.flag = 0;
+  // s.above: the smallest key above the part kept.  A bracket end is a key
+  // when finite; an open end (+inf) leaves the smallest key above the
+  // buffer, which the flat-segment rule needs for the next breakpoint
   if (g == 0) {
-    s.part = 0; s.m = si[0]; s.wpart = w5[0]; s.above = s.lo;
+    s.part = 0; s.m = si[0]; s.wpart = w5[0];
+    if (s.lo < kInf) { s.above = s.lo; s.above_ok = 1; }
   } else if (g == 1) {
     finalize(s, s.lo, mi[0], c[1], fminf(mn[0], s.above), cur);
   } else if (g == 2) {
-    s.part = 2; s.m = si[1]; s.wpart = w5[2]; s.acc = c[1]; s.above = s.hi;
+    s.part = 2; s.m = si[1]; s.wpart = w5[2]; s.acc = c[1];
+    if (s.hi < kInf) { s.above = s.hi; s.above_ok = 1; }
   } else if (g == 3) {
     finalize(s, s.hi, mi[1], c[3], fminf(mn[1], s.above), cur);
   } else {
@@ -328,6 +357,38 @@ __device__ __forceinline__ bool in_part(float kk, float lo, float hi, int part) 
   return part == 0 ? kk < lo : (part == 2 ? (kk > lo && kk < hi) : kk > hi);
 }
 
+// The key of one row: the correctly rounded quotient.  (Kept inline:
+// calling it out of line, to keep one copy of the division's code, measured
+// 4 % slower on the batched workload.)
+__device__ __forceinline__ float key_div(float r, float x) { return __fdiv_rn(r, x); }
+
+// (all G threads) the smallest key above z of the current 1-D problem:
+// rows (the quotient r_i / x_i, IEEE; only rows whose exact quotient lies
+// above z are divided), the pinned row and the special breakpoints.
+// Needed only when the cumulative weight reaches exactly half at z.
+template <int G>
+__device__ __noinline__ float min_key_above(St& s, float z) {
+  const int tid = gtid<G>();
+  float m = kInf;
+  for (int i = tid; i < s.n; i += G) {
+    const float x = s.colp[i], r = s.rr[i];
+    float k = kInf;
+    if (i == s.pq) {
+      k = -s.pbase;
+    } else if (x != 0.f) {
+      const float c = fmaf(-z, x, r);  // sign of r - z x, exact
+      if (c != 0.f && signbit(c) == signbit(x)) k = key_div(r, x);
+    }
+    if (k > z) m = fminf(m, k);
+  }
+  for (int e = tid; e < s.nspec; e += G)
+    if (s.sk[e] > z) m = fminf(m, s.sk[e]);
+  float f[1] = {0.f}, mn[1] = {m};
+  int si[1] = {0}, mi[1] = {0};
+  reduce<G, 1, 1, 1, 1>(s, f, mn, si, mi);
+  return mn[0];
+}
+
 // Weighted-median finish over the m0 elements of the selection buffer (ck,
 // cw, ids implicit = position below s.n when `first`, else cid).  acc0 is
 // the weight of all keys below the buffer's, half0 the target, above0 the
@@ -337,11 +398,12 @@ __device__ __forceinline__ bool in_part(float kk, float lo, float hi, int part) 
 // the target in place; <= 32 elements are sorted by one warp.
 template <int G>
 __device__ __noinline__ void select_buf(St& s, int m0, float cur, int first0, float acc0,
-                                        float half0, float above0, float wbuf) {
+                                        float half0, int above_ok0, float wbuf) {
   const int tid = gtid<G>(), lane = lane_id(), warp = gwarp<G>();
   gsync<G>();
   if (tid == 0) {
-    s.half = half0; s.acc = acc0; s.above = above0; s.m = m0; s.first = first0; s.flag = 0;
+    s.half = half0; s.acc = acc0; s.above = kInf; s.above_ok = above_ok0; s.m = m0;
+    s.first = first0; s.flag = 0; s.need_next = 0;
     s.wpart = wbuf;  // only steers the sample brackets
   }
   gsync<G>();
@@ -453,6 +515,11 @@ __device__ __noinline__ void select_buf(St& s, int m0, float cur, int first0, fl
     __syncwarp();
   }
   gsync<G>();
+  if (s.need_next) {  // an exact half whose next key lies outside the buffer
+    const float nx = min_key_above<G>(s, s.zstar);
+    if (tid == 0) { s.need_next = 0; flat_rule(s, s.zstar, nx, cur); }
+    gsync<G>();
+  }
 }
 
 __device__ __forceinline__ float xval(const St& s, int c, int i) {
@@ -464,16 +531,34 @@ __device__ __forceinline__ const float* colptr(const St& s, int c) {
 
 // ------------------------------------------------------------------ one-warp fused selection
 
-// Breakpoint of row i for the current 1-D problem, one formula for both:
-//   axis step:  x_i = x_ij,     key b_j + r_i / x_i  (pbase = b_j, pq = -1)
-//   polish edge: x_i = x_i . d,  key r_i / x_i        (pbase = 0), the released
-//               basis row pinned at 0; other basis rows have x_i = 0
-// weight |x_i|; x_i = 0 gives key +inf and no weight.
+// Keys are kept relative to the current value: the breakpoint of row i is
+// u_i = r_i / x_i, the point t = pbase + u_i where row i's term vanishes.
+//   axis step:   x_i = x_ij,    pbase = b_j, pq = -1
+//   polish edge: x_i = x_i . d, pbase = 0, the released basis row pinned at
+//                t = 0 (u = -pbase); other basis rows have x_i = 0
+// weight |x_i|; x_i = 0 gives key +inf and no weight.  The special
+// breakpoints (sk) are stored on the same relative scale.  Rows are placed
+// against a window by the exact sign of r_i - t x_i (one fused multiply-
+// add, see smem_rows), so the selection orders rows by their exact
+// quotients; a key itself is the correctly rounded quotient (IEEE division),
+// formed only for rows inside the window and for samples.
 __device__ __forceinline__ void row_key(const St& s, int i, float& k, float& w) {
   const float x = s.colp[i];
-  k = x != 0.f ? s.pbase + __fdividef(s.rr[i], x) : kInf;
-  if (i == s.pq) k = 0.f;
+  k = x != 0.f ? key_div(s.rr[i], x) : kInf;
+  if (i == s.pq) k = -s.pbase;
   w = fabsf(x);
+}
+
+// Where the exact quotient r / x (x != 0) lies against the window [lo, hi]:
+// r / x < lo  iff  r - lo x is nonzero with the sign opposite to x's, and
+// r / x > hi  iff  r - hi x is nonzero with x's sign.  fmaf rounds once, so
+// the sign of the exact difference survives.  Open ends (+-inf) place
+// nothing beyond them.
+__device__ __forceinline__ void place(float r, float x, float lo, float hi, bool& below,
+                                      bool& above) {
+  const float a = fmaf(-lo, x, r), c = fmaf(-hi, x, r);
+  below = a != 0.f && signbit(a) != signbit(x);
+  above = c != 0.f && signbit(c) == signbit(x);
 }
 
 // (one warp) one pass over rows and specials against the window [lo, hi]:
@@ -489,20 +574,19 @@ constexpr int kPassU = LL_PASSU;
 // path keeps its unrolled code small (instruction-cache pressure).  The
 // rows a thread visits, and their order, do not depend on it.
 template <int G>
-constexpr int kRowU = G == 32 ? LL_ROWU : 16;
+constexpr int kRowU = kSmemCols<G> ? LL_ROWU : 16;
 
 // The buffer pointers are passed in registers (restrict-qualified): going
 // through the shared state struct would reload them after every store.
 __device__ __forceinline__ void classify_one(float* __restrict__ bk, float* __restrict__ bw,
                                              int* __restrict__ bi, float k, float w, int id,
                                              bool valid, float lo, float hi, float& al, float& ale,
-                                             float& at, float& amin, int& base, int cap) {
+                                             float& at, int& base, int cap) {
   const int lane = lane_id();
   at += w;
   if (k < lo) al += w;
   if (k <= hi) ale += w;
   const bool in = valid && k >= lo && k <= hi;
-  if (k > hi) amin = fminf(amin, k);
   const unsigned msk = __ballot_sync(0xffffffffu, in);
   const int pos = base + __popc(msk & ((1u << lane) - 1u));
   if (in && pos < cap) { bk[pos] = k; bw[pos] = w; bi[pos] = id; }
@@ -510,16 +594,21 @@ __device__ __forceinline__ void classify_one(float* __restrict__ bk, float* __re
 }
 
 // Rows from shared memory (a per-row factor x_i and the residual r_i):
-//   axis step:   x_i = x_ij,     z = b_j + r_i / x_i, weight |x_i|  (bj = b_j, qc = -1)
-//   polish edge: x_i = x_i . d,  t = r_i / x_i (0 for the released row qc)  (bj = 0)
+//   axis step:   x_i = x_ij,    key u_i = r_i / x_i on the scale relative
+//                to b_j (pb = b_j, qc = -1), weight |x_i|
+//   polish edge: x_i = x_i . d, key u_i = r_i / x_i (pb = 0), the released
+//                row qc pinned at -pb
+// Each row is placed against the window [lo, hi] without a division
+// (place); the correctly rounded key is formed only for rows inside it.
 // Batches of 32 * kPassU rows; the compaction code runs only when some lane
 // of the warp holds a key inside the window.
-__device__ __forceinline__ void smem_rows(uint32_t col_s, uint32_t rr_s, float bj, int qc, int n,
+__device__ __forceinline__ void smem_rows(uint32_t col_s, uint32_t rr_s, float pb, int qc, int n,
                                           float lo, float hi, uint32_t bk_s, uint32_t bw_s,
                                           uint32_t bi_s, float& al, float& ale, float& at,
-                                          float& amin, int& base) {
+                                          int& base) {
   const int lane = lane_id();
   const unsigned lt = (1u << lane) - 1u;
+  const float qk = -pb;  // key of the pinned row
   for (int i0 = 0; i0 < n; i0 += 32 * kPassU) {
     float xv[kPassU], rv[kPassU];
 #pragma unroll
@@ -532,20 +621,21 @@ __device__ __forceinline__ void smem_rows(uint32_t col_s, uint32_t rr_s, float b
     for (int u = 0; u < kPassU; ++u) {
       if (i0 + u * 32 >= n) break;  // uniform
       const int e = i0 + u * 32 + lane;
-      const float x = xv[u];  // zero beyond n: no weight, key +inf
+      const float x = xv[u], r = rv[u];  // x zero beyond n: no weight, no key
       const float w = fabsf(x);
-      float k = x != 0.f ? bj + __fdividef(rv[u], x) : kInf;
-      if (e == qc) k = 0.f;
+      bool below, above;
+      place(r, x, lo, hi, below, above);
+      const bool pin = e == qc;
+      if (pin) { below = qk < lo; above = qk > hi; }
       at += w;
-      al += k < lo ? w : 0.f;
-      ale += k <= hi ? w : 0.f;
-      amin = k > hi ? fminf(amin, k) : amin;
-      const bool in = e < n && k >= lo && k <= hi;
+      al += below ? w : 0.f;
+      ale += above ? 0.f : w;
+      const bool in = e < n && (pin || x != 0.f) && !below && !above;
       const unsigned msk = __ballot_sync(0xffffffffu, in);
       if (msk) {
         const int pos = base + __popc(msk & lt);
         if (in && pos < kBufCap) {
-          sts_f(bk_s + 4u * pos, k);
+          sts_f(bk_s + 4u * pos, pin ? qk : key_div(r, x));
           sts_f(bw_s + 4u * pos, w);
           sts_i(bi_s + 4u * pos, e);
         }
@@ -561,11 +651,11 @@ __device__ __noinline__ void fused_pass(St& s, float lo, float hi) {
   float* __restrict__ bk = s.ck;
   float* __restrict__ bw = s.cw;
   int* __restrict__ bi = s.cid;
-  float al = 0.f, ale = 0.f, at = 0.f, amin = kInf;
+  float al = 0.f, ale = 0.f, at = 0.f;
   int base = 0;
   // one warp: the per-row factors are in shared memory (a column buffer)
   smem_rows(smem_u32(s.colp), smem_u32(s.rr), s.pbase, s.pq, n, lo, hi, smem_u32(bk),
-            smem_u32(bw), smem_u32(bi), al, ale, at, amin, base);
+            smem_u32(bw), smem_u32(bi), al, ale, at, base);
   const float* __restrict__ sk = s.sk;
   const float* __restrict__ sw = s.sw;
   const int* __restrict__ sid = s.sid;
@@ -573,14 +663,13 @@ __device__ __noinline__ void fused_pass(St& s, float lo, float hi) {
     const int e = j0 + lane;
     const bool v = e < nspec;
     classify_one(bk, bw, bi, v ? sk[e] : kInf, v ? sw[e] : 0.f, v ? sid[e] : 0, v, lo, hi, al,
-                 ale, at, amin, base, kBufCap);
+                 ale, at, base, kBufCap);
   }
   al = warp_sum(al);
   ale = warp_sum(ale);
   at = warp_sum(at);
-  amin = warp_min(amin);
   __syncwarp();
-  if (lane == 0) { s.p_wl = al; s.p_wi = ale; s.p_wt = at; s.p_cnt = base; s.p_amin = amin; }
+  if (lane == 0) { s.p_wl = al; s.p_wi = ale; s.p_wt = at; s.p_cnt = base; }
   __syncwarp();
 }
 
@@ -595,7 +684,10 @@ __device__ __noinline__ void window_from_samples(St& s, float k, float w, float 
   const bool ok = k > rl && k < ru && w > 0.f;
   if (!ok) { k = kInf; w = 0.f; }
   const int cnt = __popc(__ballot_sync(0xffffffffu, ok));
-  float lo = next_up(rl), hi = next_down(ru);
+  // too few samples: the closed window [rl, ru].  Rows are placed by their
+  // exact quotients, and the target may lie strictly between rl and the
+  // next float (or ru and the float before it), where no key value exists
+  float lo = rl, hi = ru;
   if (cnt >= 8) {
     int id = lane;
     warp_sort(k, w, id);  // inside samples first, in key order
@@ -665,7 +757,7 @@ __device__ __noinline__ void select_fused(St& s, float cur, bool prior, float lo
       rl = hi; wrl = wle;
       region_window(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
     } else if (cnt <= kBufCap) {            // target inside, all keys buffered
-      select_buf<32>(s, cnt, cur, 0, wl, half, s.p_amin, wle - wl);
+      select_buf<32>(s, cnt, cur, 0, wl, half, hi == kInf, wle - wl);
       return;
     } else {                                // inside but too many keys: narrow
       rl = next_down(lo); ru = next_up(hi); wrl = wl; wru = wle;
@@ -673,7 +765,7 @@ __device__ __noinline__ void select_fused(St& s, float cur, bool prior, float lo
       if (s.lo == lo && s.hi == hi) {
         // no narrower window from the samples (keys tie at the ends): finish
         // on the buffered keys, which begin the window in row order
-        select_buf<32>(s, kBufCap, cur, 0, wl, half, s.p_amin, wle - wl);
+        select_buf<32>(s, kBufCap, cur, 0, wl, half, hi == kInf, wle - wl);
         return;
       }
     }
@@ -689,7 +781,7 @@ __device__ __noinline__ void select_fused(St& s, float cur, bool prior, float lo
 //
 // The same windowed weighted median with W = G / 32 warps sharing one fit
 // (long problems): warp w takes the row batches w, w + W, w + 2W, ... of
-// 32 * kPassU rows and compacts its keys inside the window into its own
+// 32 * kPU rows (kPU rows per lane) and compacts its keys inside the window into its own
 // sub-buffer of kSubCap entries; per-warp sums are combined in warp order.
 // The per-row factor (the column for axis steps, the edge products for the
 // polish) is read from global memory, the residual from shared memory.
@@ -700,6 +792,8 @@ __device__ __noinline__ void fused_pass_blk(St& s, float lo, float hi) {
   const int lane = lane_id(), warp = gwarp<G>(), tid = gtid<G>();
   const int n = s.n, nspec = s.nspec;
   const float* __restrict__ xs = s.colp;
+  uint32_t col_s = 0u;
+  if constexpr (kSmemCols<G>) col_s = smem_u32(xs);
   const float bj = s.pbase;
   const int qc = s.pq;
   const uint32_t rr_s = smem_u32(s.rr);
@@ -708,34 +802,40 @@ __device__ __noinline__ void fused_pass_blk(St& s, float lo, float hi) {
   int* __restrict__ bi = s.cid + warp * kSubCap;
   const uint32_t bk_s = smem_u32(bk), bw_s = smem_u32(bw), bi_s = smem_u32(bi);
   const unsigned lt = (1u << lane) - 1u;
-  float al = 0.f, ale = 0.f, at = 0.f, amin = kInf;
+  float al = 0.f, ale = 0.f, at = 0.f;
   int base = 0;
-  for (int i0 = warp * 32 * kPassU; i0 < n; i0 += G * kPassU) {
-    float xv[kPassU], rv[kPassU];
+  const float qk = -bj;  // key of the pinned row
+  // rows per lane per batch: columns read from global memory (the block
+  // shape) keep four loads in flight, shared-memory columns two
+  constexpr int kPU = kSmemCols<G> ? kPassU : 4;
+  for (int i0 = warp * 32 * kPU; i0 < n; i0 += G * kPU) {
+    float xv[kPU], rv[kPU];
 #pragma unroll
-    for (int u = 0; u < kPassU; ++u) {
+    for (int u = 0; u < kPU; ++u) {
       const int e = i0 + u * 32 + lane;
-      xv[u] = e < n ? ldg_f(xs + e) : 0.f;
+      if constexpr (kSmemCols<G>) xv[u] = e < n ? lds_f(col_s + 4u * e) : 0.f;
+      else xv[u] = e < n ? ldg_f(xs + e) : 0.f;
       rv[u] = e < n ? lds_f(rr_s + 4u * e) : 0.f;
     }
 #pragma unroll
-    for (int u = 0; u < kPassU; ++u) {
+    for (int u = 0; u < kPU; ++u) {
       if (i0 + u * 32 >= n) break;  // uniform
       const int e = i0 + u * 32 + lane;
-      const float x = xv[u];  // zero beyond n: no weight, key +inf
+      const float x = xv[u], r = rv[u];  // x zero beyond n: no weight, no key
       const float w = fabsf(x);
-      float k = x != 0.f ? bj + __fdividef(rv[u], x) : kInf;
-      if (e == qc) k = 0.f;
+      bool below, above;
+      place(r, x, lo, hi, below, above);
+      const bool pin = e == qc;
+      if (pin) { below = qk < lo; above = qk > hi; }
       at += w;
-      al += k < lo ? w : 0.f;
-      ale += k <= hi ? w : 0.f;
-      amin = k > hi ? fminf(amin, k) : amin;
-      const bool in = e < n && k >= lo && k <= hi;
+      al += below ? w : 0.f;
+      ale += above ? 0.f : w;
+      const bool in = e < n && (pin || x != 0.f) && !below && !above;
       const unsigned msk = __ballot_sync(0xffffffffu, in);
       if (msk) {
         const int pos = base + __popc(msk & lt);
         if (in && pos < kSubCap) {
-          sts_f(bk_s + 4u * pos, k);
+          sts_f(bk_s + 4u * pos, pin ? qk : key_div(r, x));
           sts_f(bw_s + 4u * pos, w);
           sts_i(bi_s + 4u * pos, e);
         }
@@ -748,35 +848,32 @@ __device__ __noinline__ void fused_pass_blk(St& s, float lo, float hi) {
       const int e = j0 + lane;
       const bool v = e < nspec;
       classify_one(bk, bw, bi, v ? s.sk[e] : kInf, v ? s.sw[e] : 0.f, v ? s.sid[e] : 0, v, lo, hi,
-                   al, ale, at, amin, base, kSubCap);
+                   al, ale, at, base, kSubCap);
     }
   }
   al = warp_sum(al);
   ale = warp_sum(ale);
   at = warp_sum(at);
-  amin = warp_min(amin);
   if (lane == 0) {
     s.redf[warp * 16 + 0] = al;
     s.redf[warp * 16 + 1] = ale;
     s.redf[warp * 16 + 2] = at;
-    s.redf[warp * 16 + 3] = amin;
     s.wcnt[warp] = base;
   }
-  __syncthreads();
+  gsync<G>();
   if (tid == 0) {
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = kInf;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
     int c = 0, ov = 0;
     for (int w = 0; w < W; ++w) {
       a0 += s.redf[w * 16 + 0];
       a1 += s.redf[w * 16 + 1];
       a2 += s.redf[w * 16 + 2];
-      a3 = fminf(a3, s.redf[w * 16 + 3]);
       c += s.wcnt[w];
       ov |= s.wcnt[w] > kSubCap;
     }
-    s.p_wl = a0; s.p_wi = a1; s.p_wt = a2; s.p_amin = a3; s.p_cnt = c; s.p_ovf = ov;
+    s.p_wl = a0; s.p_wi = a1; s.p_wt = a2; s.p_cnt = c; s.p_ovf = ov;
   }
-  __syncthreads();
+  gsync<G>();
 }
 
 // Move the buffered keys of every warp (up to kSubCap each) to the front of
@@ -803,13 +900,13 @@ __device__ __forceinline__ int compact_sub(St& s) {
       id[u] = s.cid[warp * kSubCap + e];
     }
   }
-  __syncthreads();
+  gsync<G>();
 #pragma unroll
   for (int u = 0; u < kPer; ++u) {
     const int e = u * 32 + lane;
     if (e < c) { s.ck[pre + e] = k[u]; s.cw[pre + e] = wv[u]; s.cid[pre + e] = id[u]; }
   }
-  __syncthreads();
+  gsync<G>();
   return tot;
 }
 
@@ -847,7 +944,7 @@ __device__ __noinline__ void select_fused_blk(St& s, float cur, bool prior, floa
   for (int it = 0; it < kMaxPasses; ++it) {
     fused_pass_blk<G>(s, lo, hi);
     if (tid == 0) s.passes++;
-    const float wl = s.p_wl, wle = s.p_wi, wt = s.p_wt, amin = s.p_amin;
+    const float wl = s.p_wl, wle = s.p_wi, wt = s.p_wt;
     const int cnt = s.p_cnt, ovf = s.p_ovf;
     if (half < 0.f) {
       if (!(wt > 0.f)) {
@@ -867,7 +964,7 @@ __device__ __noinline__ void select_fused_blk(St& s, float cur, bool prior, floa
       if (warp == 0) region_window(s, rl, ru, (half - wrl) / fmaxf(wru - wrl, 1e-30f), 0);
     } else if (!ovf) {                      // target inside, all keys buffered
       compact_sub<G>(s);
-      select_buf<G>(s, cnt, cur, 0, wl, half, amin, wle - wl);
+      select_buf<G>(s, cnt, cur, 0, wl, half, hi == kInf, wle - wl);
       return;
     } else {                                // inside but too many keys: narrow
       rl = next_down(lo); ru = next_up(hi); wrl = wl; wru = wle;
@@ -877,7 +974,7 @@ __device__ __noinline__ void select_fused_blk(St& s, float cur, bool prior, floa
         // no narrower window from the samples (keys tie at the ends): finish
         // on the buffered keys
         const int m = compact_sub<G>(s);
-        select_buf<G>(s, m, cur, 0, wl, half, amin, wle - wl);
+        select_buf<G>(s, m, cur, 0, wl, half, hi == kInf, wle - wl);
         return;
       }
     }
@@ -997,10 +1094,11 @@ __device__ __noinline__ bool lu(St& s) {
     float pv = B[k * p + k];
     for (int i = k + 1 + lane; i < p; i += 32) B[i * p + k] /= pv;
     __syncwarp();
-    int rem = p - k - 1;
-    for (int e = lane; e < rem * rem; e += 32) {
-      int i = k + 1 + e / rem, c = k + 1 + e % rem;
-      B[i * p + c] -= B[i * p + k] * B[k * p + c];
+    // trailing update, rows in turn, lanes over columns (no index division)
+    for (int i = k + 1; i < p; ++i) {
+      const float l = B[i * p + k];
+      if (l != 0.f)
+        for (int c = k + 1 + lane; c < p; c += 32) B[i * p + c] -= l * B[k * p + c];
     }
     __syncwarp();
   }
@@ -1121,7 +1219,7 @@ __device__ __noinline__ bool lu_blk(St& s) {
       }
       if (lane == 0) { s.m = bi; s.flag = bvv > 1e-7f * am; }
     }
-    __syncthreads();
+    gsync<G>();
     if (!s.flag) return false;  // uniform
     const int bi = s.m;
     if (bi != k) {
@@ -1130,16 +1228,17 @@ __device__ __noinline__ bool lu_blk(St& s) {
       }
       if (tid == 0) { int t = s.perm[k]; s.perm[k] = s.perm[bi]; s.perm[bi] = t; }
     }
-    __syncthreads();
+    gsync<G>();
     const float pv = B[k * p + k];
     for (int i = k + 1 + tid; i < p; i += G) B[i * p + k] /= pv;
-    __syncthreads();
-    const int rem = p - k - 1;
-    for (int e = tid; e < rem * rem; e += G) {
-      const int i = k + 1 + e / rem, c = k + 1 + e % rem;
-      B[i * p + c] -= B[i * p + k] * B[k * p + c];
+    gsync<G>();
+    // trailing update: warps over rows, lanes over columns (no index division)
+    for (int i = k + 1 + warp; i < p; i += G / 32) {
+      const float l = B[i * p + k];
+      if (l != 0.f)
+        for (int c = k + 1 + lane; c < p; c += 32) B[i * p + c] -= l * B[k * p + c];
     }
-    __syncthreads();
+    gsync<G>();
   }
   return true;
 }
@@ -1151,7 +1250,7 @@ template <int G>
 __device__ __noinline__ void refine_blk(St& s, float* x, const float* h, bool trans) {
   constexpr int W = G / 32;
   const int lane = lane_id(), warp = gwarp<G>(), p = s.p;
-  __syncthreads();
+  gsync<G>();
   for (int e = warp; e < p; e += W) {
     double acc = 0.0;
     if (!trans) {
@@ -1171,36 +1270,37 @@ __device__ __noinline__ void refine_blk(St& s, float* x, const float* h, bool tr
     acc = warp_sum_d(acc);
     if (lane == 0) s.rv[e] = (float)((double)h[e] - acc);
   }
-  __syncthreads();
+  gsync<G>();
   if (warp == 0) {
     if (trans) lu_solve_t(s, s.rv);
     else lu_solve(s, s.rv);
     for (int e = lane; e < p; e += 32) x[e] += s.rv[e];
   }
-  __syncthreads();
+  gsync<G>();
 }
 
 // (one warp) form the basis matrix, factor it and snap b onto the basis
 // hyperplanes (phantom coordinates keep their value).  Sets s.flag.
 __device__ __noinline__ void snap(St& s) {
-  const int lane = lane_id(), p = s.p, pp = p * p;
+  const int lane = lane_id(), p = s.p;
   // basis matrix rows = constraint normals; element (k, c) of a row
-  // constraint is x_{code_k, c}: strided loads, issued 8 per lane at a time
-  for (int e0 = 0; e0 < pp; e0 += 32 * 8) {
-    float v[8];
+  // constraint is x_{code_k, c}: strided loads, eight rows at a time so
+  // that eight loads per lane are in flight
+  for (int k0 = 0; k0 < p; k0 += 8) {
+    for (int c = lane; c < p; c += 32) {
+      float v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * 32 + lane;
-      v[u] = 0.f;
-      if (e < pp) {
-        const int k = e / p, c = e - k * p, cd = s.code[k];
-        v[u] = cd >= 0 ? xval(s, c, cd) : (c == -cd - 1 ? 1.f : 0.f);
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + u;
+        v[u] = 0.f;
+        if (k < p) {
+          const int cd = s.code[k];
+          v[u] = cd >= 0 ? xval(s, c, cd) : (c == -cd - 1 ? 1.f : 0.f);
+        }
       }
-    }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * 32 + lane;
-      if (e < pp) s.Bm[e] = v[u];
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < p) s.Bm[(k0 + u) * p + c] = v[u];
     }
   }
   for (int k = lane; k < p; k += 32) {
@@ -1231,10 +1331,17 @@ __device__ __noinline__ void snap_g(St& s) {
     snap(s);
     return;
   }
-  const int tid = gtid<G>(), warp = gwarp<G>(), p = s.p, pp = p * p;
-  for (int e = tid; e < pp; e += G) {
-    const int k = e / p, c = e - k * p, cd = s.code[k];
-    s.Bm[e] = cd >= 0 ? xval(s, c, cd) : (c == -cd - 1 ? 1.f : 0.f);
+  if (kSmemCols<G>) {  // small groups: p <= 256 algebra on warp 0
+    if (gwarp<G>() == 0) snap(s);
+    gsync<G>();
+    return;
+  }
+  const int tid = gtid<G>(), warp = gwarp<G>(), lane = lane_id(), p = s.p;
+  for (int k = warp; k < p; k += G / 32) {  // warps over rows, lanes over columns
+    const int cd = s.code[k];
+#pragma unroll 4
+    for (int c = lane; c < p; c += 32)
+      s.Bm[k * p + c] = cd >= 0 ? xval(s, c, cd) : (c == -cd - 1 ? 1.f : 0.f);
   }
   for (int k = tid; k < p; k += G) {
     const int cd = s.code[k];
@@ -1242,19 +1349,19 @@ __device__ __noinline__ void snap_g(St& s) {
     s.hv[k] = h;
     s.mu[k] = h;  // right-hand side (mu is free here)
   }
-  __syncthreads();
+  gsync<G>();
   const bool ok = lu_blk<G>(s);  // group-uniform
   if (ok) {
     if (warp == 0) lu_solve(s, s.hv);
     refine_blk<G>(s, s.hv, s.mu, false);
     for (int c = tid; c < p; c += G) s.bv[c] = s.hv[c];
-    __syncthreads();
+    gsync<G>();
     for (int k = tid; k < p; k += G)
       if (s.code[k] < 0 && !s.phan[k]) s.bv[-s.code[k] - 1] = 0.f;
   }
-  __syncthreads();
+  gsync<G>();
   if (tid == 0) s.flag = ok;
-  __syncthreads();
+  gsync<G>();
 }
 
 // (one warp) multipliers from the column sums in red2: right-hand side
@@ -1431,13 +1538,14 @@ __device__ __forceinline__ void edge_products(St& s, float* __restrict__ vd) {
   }
 }
 
-// (one warp) start copying column j into column buffer `buf` (16-byte
-// asynchronous copies; the gathered column is 16-byte aligned and padded
-// to a multiple of 4 floats).
-__device__ __forceinline__ void prefetch_col(St& s, int j, int buf) {
+// (all G threads) start copying column j into column buffer `buf` with
+// 16-byte asynchronous copies (the gathered column is 16-byte aligned and
+// padded to a multiple of 4 floats); wait with cp_async_wait_all.
+template <int G>
+__device__ __forceinline__ void prefetch_all(St& s, int j, int buf) {
   const float* src = s.Xq + (int64_t)j * s.ld;
   const uint32_t dst = smem_u32(s.cb[buf]);
-  for (int q = lane_id(); q < (s.ld >> 2); q += 32) cp_async16(dst + 16u * q, src + 4 * q);
+  for (int q = gtid<G>(); q < (s.ld >> 2); q += G) cp_async16(dst + 16u * q, src + 4 * q);
   cp_async_commit();
 }
 
@@ -1460,11 +1568,13 @@ template <int G>
 __device__ __noinline__ float axis_update(St& s, int j, int jnext) {
   const float bj = s.bv[j];
   const float* col = colptr(s, j);
-  if (G == 32) {
-    // the column of this step was prefetched into cb[cur]; start the next
+  if (kSmemCols<G>) {
+    // the column of this step was copied into cb[cur] (each thread's share;
+    // the barrier makes all of it visible); start the next column's copy
+    // into the other buffer (read by no one since the last step's barrier)
     cp_async_wait_all();
-    __syncwarp();
-    if (jnext >= 0) prefetch_col(s, jnext, s.cur ^ 1);
+    gsync<G>();
+    if (jnext >= 0) prefetch_all<G>(s, jnext, s.cur ^ 1);
     col = s.cb[s.cur];
   } else if (jnext >= 0) {
     // block path: the columns stream from global memory; pull the next
@@ -1479,15 +1589,16 @@ __device__ __noinline__ float axis_update(St& s, int j, int jnext) {
     s.pbase = bj;
     s.pq = -1;
     s.nspec = s.lam > 0.f ? 1 : 0;
-    s.sk[0] = 0.f; s.sw[0] = s.lam; s.sid[0] = coord_code(j);
+    s.sk[0] = -bj; s.sw[0] = s.lam; s.sid[0] = coord_code(j);  // the penalty's breakpoint 0
   }
   gsync<G>();
   {
+    // keys relative to b_j: the current value is 0, the window [-dl, dl]
     const float dl = s.dl[j];
-    if (G == 32) select_fused(s, bj, true, bj - dl, bj + dl);
-    else select_fused_blk<G>(s, bj, true, bj - dl, bj + dl);
+    if (G == 32) select_fused(s, 0.f, true, -dl, dl);
+    else select_fused_blk<G>(s, 0.f, true, -dl, dl);
   }
-  const float z = s.zstar;
+  const float z = bj + s.zstar;
   const int own = s.owner;
   const float d = z - bj;
   if (d != 0.f) axpy_r<G>(s, col, d);
@@ -1496,7 +1607,7 @@ __device__ __noinline__ float axis_update(St& s, int j, int jnext) {
     s.bv[j] = z;
     s.piv[j] = own == kNone ? -2 : (own < 0 ? -1 : own);
     s.dl[j] = fmaxf(kDlf * fabsf(d), 1e-5f * fmaxf(1.f, fabsf(z)));
-    if (G == 32) s.cur ^= 1;
+    if (kSmemCols<G>) s.cur ^= 1;
   }
   gsync<G>();
   return d;
@@ -1509,12 +1620,12 @@ __device__ __noinline__ int ccd(St& s, int skip, int max_sweeps) {
   const int p = s.p;
   const int j0 = skip == 0 ? 1 : 0;  // first axis of a sweep
   if (j0 >= p) return 1;              // nothing to move
-  if (G == 32) {
-    cp_async_wait_all();  // no copy may still target a buffer
-    __syncwarp();
-    if (lane_id() == 0) s.cur = 0;
-    __syncwarp();
-    prefetch_col(s, j0, 0);
+  if (kSmemCols<G>) {
+    cp_async_wait_all();
+    gsync<G>();
+    if (gtid<G>() == 0) s.cur = 0;
+    gsync<G>();
+    prefetch_all<G>(s, j0, 0);
   }
   for (int sw = 1; sw <= max_sweeps; ++sw) {
     float mx = 0.f;
@@ -1765,10 +1876,7 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
   *is_opt = 0;
   *nonunique = 0;
   if (tid == 0) s.bland = 0;
-  if (G == 32) {
-    cp_async_wait_all();  // the column buffers hold edge products below
-    __syncwarp();
-  }
+  if (kSmemCols<G>) { cp_async_wait_all(); gsync<G>(); }
   if (warp == 0) basis_seen(s, 0);  // the starting basis
   gsync<G>();
   nh = 1;
@@ -1816,7 +1924,7 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     }
     gsync<G>();
     {
-      float* vd = G == 32 ? s.cb[0] : s.vdg;
+      float* vd = kSmemCols<G> ? s.cb[0] : s.vdg;
       edge_products<G>(s, vd);
       gsync<G>();
       if (tid == 0) { s.colp = vd; s.pbase = 0.f; s.pq = s.qcode; }
@@ -1979,12 +2087,12 @@ __device__ __forceinline__ void run_problem(St& s, int q, int ncap) {
           if (!isfinite(v)) bad = 1;
           tile[c * 33 + i] = v;
         }
-        __syncthreads();
+        gsync<G>();
         for (int e = tid; e < p * 32; e += G) {
           const int c = e >> 5, i = e & 31;
           if (i < rows) Xw[(int64_t)c * ld + i0 + i] = tile[c * 33 + i];
         }
-        __syncthreads();
+        gsync<G>();
       }
     }
     for (int i = tid; i < n; i += G) if (!isfinite(A.y[o0 + i])) bad = 1;
@@ -2093,7 +2201,7 @@ __host__ __device__ size_t group_smem_bytes(int ncap, int P) {
   // gather also stages 32 x P tiles there
   size_t sel_bm = 3 * cap > (size_t)P * P ? 3 * cap : (size_t)P * P;
   if (G > 32 && sel_bm < 33 * (size_t)P) sel_bm = 33 * (size_t)P;
-  size_t colbuf = G == 32 ? 2 * (size_t)ncap : 0;
+  size_t colbuf = kSmemCols<G> ? 2 * (size_t)ncap : 0;
   size_t words = (size_t)ncap + colbuf + sel_bm + 7 * (size_t)P + (size_t)W * P +
                  9 * (size_t)P + 3 * ((size_t)P + 1) + (size_t)ncap / 32 + 1 +
                  2 * (size_t)W * 16 + 64 + W + kHist;
@@ -2111,7 +2219,7 @@ __device__ void carve(St& s, unsigned char* raw, int ncap, int P) {
   s.pbase = 0.f;
   float* f = reinterpret_cast<float*>(raw);
   s.rr = f; f += ncap;
-  if (G == 32) { s.cb[0] = f; f += ncap; s.cb[1] = f; f += ncap; }
+  if (kSmemCols<G>) { s.cb[0] = f; f += ncap; s.cb[1] = f; f += ncap; }
   else { s.cb[0] = s.cb[1] = nullptr; }
   float* sel = f;
   s.ck = f; f += s.cap;
@@ -2175,6 +2283,8 @@ __global__ void __launch_bounds__(G * NW) fit_block_kernel(FitArgs args, int nca
     gsync<G>();
     if (q >= A.B) break;
     run_problem<G>(s, q, ncap);
+    // no copy may outlive the problem (or the block)
+    if (kSmemCols<G>) cp_async_wait_all();
     gsync<G>();
   }
 }
@@ -2207,7 +2317,10 @@ int fit_block_max_rows(int G, int P) {
   int lo = 0, hi = 1 << 16;
   while (lo < hi) {
     int mid = (lo + hi + 1) / 2;
-    size_t b = G == 32 ? group_smem_bytes<32>(mid, P) : group_smem_bytes<kBlockG>(mid, P);
+    size_t b = G == 32    ? group_smem_bytes<32>(mid, P)
+               : G == 64  ? group_smem_bytes<64>(mid, P)
+               : G == 128 ? group_smem_bytes<128>(mid, P)
+                          : group_smem_bytes<kBlockG>(mid, P);
     if (b <= limit) lo = mid; else hi = mid - 1;
   }
   return lo;
@@ -2230,7 +2343,8 @@ int launch_group(const ladlasso_dims* d) {
       G = kBlockG;
     return G;
   }
-  return d->group_threads == 32 || d->group_threads == kBlockG ? d->group_threads : 0;
+  const int g = d->group_threads;
+  return g == 32 || g == 64 || g == 128 || g == kBlockG ? g : 0;
 }
 
 static int row_cap(int n_max) {
@@ -2242,10 +2356,13 @@ static int row_cap(int n_max) {
 // shared memory allows (at most 16, at most `fits_per_block` when > 0);
 // one block per fit otherwise.
 int fit_block_fits_per_block(int G, int P, int n_max, int fits_per_block) {
-  if (G != 32) return 1;
-  const size_t per = group_smem_bytes<32>(row_cap(n_max), P);
+  if (G == kBlockG) return 1;
+  const int ncap = row_cap(n_max);
+  const size_t per = G == 32 ? group_smem_bytes<32>(ncap, P)
+                     : G == 64 ? group_smem_bytes<64>(ncap, P)
+                               : group_smem_bytes<128>(ncap, P);
   int nw = (int)(kDynSmemLimit / (per ? per : 1));
-  if (nw > 16) nw = 16;
+  if (nw > 512 / G) nw = 512 / G;  // at most 512 threads a block
   if (fits_per_block > 0 && nw > fits_per_block) nw = fits_per_block;
   return nw < 1 ? 1 : nw;
 }
@@ -2253,10 +2370,20 @@ int fit_block_fits_per_block(int G, int P, int n_max, int fits_per_block) {
 cudaError_t launch_fit_block(const FitArgs& a, cudaStream_t st, int num_sms, int G,
                              int fits_per_block) {
   const int ncap = row_cap(a.n_max);
+  int nw = G == kBlockG ? 1 : fit_block_fits_per_block(G, a.P, a.n_max, fits_per_block);
+  if (fits_per_block == 0 && G != kBlockG) {
+    // automatic: a problem set with fewer problems than the SMs can hold
+    // spreads over every SM instead of filling a few blocks
+    const int spread = (int)(((int64_t)a.B + num_sms - 1) / num_sms);
+    if (spread < nw) nw = spread < 1 ? 1 : spread;
+  }
   switch (G) {
     case 32:
-      return launch_variant<32, 16>(a, st, num_sms, ncap,
-                                    fit_block_fits_per_block(32, a.P, a.n_max, fits_per_block));
+      return launch_variant<32, 16>(a, st, num_sms, ncap, nw);
+    case 64:
+      return launch_variant<64, 8>(a, st, num_sms, ncap, nw);
+    case 128:
+      return launch_variant<128, 4>(a, st, num_sms, ncap, nw);
     case kBlockG: return launch_variant<kBlockG, 1>(a, st, num_sms, ncap, 1);
     default: return cudaErrorInvalidValue;
   }

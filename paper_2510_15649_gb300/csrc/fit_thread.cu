@@ -138,7 +138,7 @@ struct TFit {
     int* __restrict__ i_ = zi;
     for (int i = 0; i < n; ++i) {
       float xv = col[i];
-      if (xv != 0.f) { k_[m] = bj + __fdividef(rr[i], xv); w_[m] = fabsf(xv); i_[m] = i; ++m; }
+      if (xv != 0.f) { k_[m] = bj + __fdiv_rn(rr[i], xv); w_[m] = fabsf(xv); i_[m] = i; ++m; }
     }
     if (lam > 0.f) { zk[m] = 0.f; zw[m] = lam; zi[m] = coord_code(j); ++m; }
     int own;
@@ -465,7 +465,7 @@ struct TFit {
         float v = 0.f;
         for (int c = 0; c < p; ++c) v += x(i, c) * dv[c];
         if (i == qcode) { zk[m] = 0.f; zw[m] = fabsf(v); zi[m] = i; ++m; }
-        else if (v != 0.f) { zk[m] = __fdividef(r[i], v); zw[m] = fabsf(v); zi[m] = i; ++m; }
+        else if (v != 0.f) { zk[m] = __fdiv_rn(r[i], v); zw[m] = fabsf(v); zi[m] = i; ++m; }
       }
       for (int c = 0; c < p; ++c) {
         int kk = -1;

@@ -1,8 +1,11 @@
 """Multi-process layout: one process per GPU, independent problems.
 
-Fits are independent, so the batch shards across ranks with no collective on
-the data path; the only collectives are a barrier around the timed region and
-the max of the step times (so the slowest rank sets the job time).
+Fits are independent, so a batch shards across ranks with no collective on
+the data path (by problem count or by cost, contiguous shares), and serving
+requests are routed to per-GPU slot pools by load (route_requests); the only
+collectives are a barrier around the timed region, the max of the step
+times (so the slowest rank sets the job time) and sums or gathers of
+counts and latencies for the report.
 """
 from __future__ import annotations
 
@@ -69,6 +72,60 @@ def shard_batch(batch: dict, lo: int, hi: int) -> dict:
     else:
         out["row_idx"] = ri[a:b]
     return out
+
+
+def cost_share(batch: dict, L: int, rank: int, world: int) -> tuple:
+    """This rank's share of one batch for strong scaling: contiguous
+    problems balanced by n * p * L (cost_shard_range), cut out with
+    shard_batch.  Returns (the share as a batch, (lo, hi))."""
+    import numpy as np
+    cost = np.diff(np.asarray(batch["offsets"], np.int64)).astype(np.float64) \
+        * np.asarray(batch["p"], np.float64) * L
+    lo, hi = cost_shard_range(cost, rank, world)
+    return shard_batch(batch, lo, hi), (lo, hi)
+
+
+def covered_once(lo: int, hi: int, B: int, dist=None, device=None) -> bool:
+    """True when the ranks' shares [lo, hi) of B problems cover every
+    problem exactly once (a sum over ranks of each rank's indicator)."""
+    import torch
+    t = torch.zeros(B, dtype=torch.int32, device=device if device is not None else "cpu")
+    t[lo:hi] = 1
+    if dist is not None and dist.is_available() and dist.is_initialized():
+        dist.all_reduce(t)
+    return bool(torch.all(t == 1).item())
+
+
+def route_requests(sizes, world: int) -> "np.ndarray":
+    """Rank (GPU) for each serving request, in arrival order: the rank with
+    the least work routed to it so far (ties to the lowest rank), the work
+    of a request being its size (e.g. n * p, the design it fits along its
+    path).  Deterministic, so every rank computes the same routing from the
+    same trace with no exchange; each rank then serves its own requests in
+    its own slot pool."""
+    import numpy as np
+    if world < 1:
+        raise ValueError("bad world size")
+    w = np.asarray(sizes, np.float64)
+    if w.ndim != 1 or np.any(w < 0) or not np.all(np.isfinite(w)):
+        raise ValueError("sizes must be a finite non-negative vector")
+    load = np.zeros(world)
+    out = np.empty(len(w), np.int64)
+    for i, c in enumerate(w):
+        r = int(np.argmin(load))
+        out[i] = r
+        load[r] += c
+    return out
+
+
+def gather_lists(values: list, dist=None) -> list:
+    """Concatenation, in rank order, of every rank's list (the list itself
+    without a process group); host objects, for statistics."""
+    if dist is None or not dist.is_available() or not dist.is_initialized():
+        return list(values)
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, list(values))
+    return [v for part in parts for v in part]
 
 
 def max_over_ranks(value: float, dist=None, device=None) -> float:

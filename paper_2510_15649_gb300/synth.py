@@ -143,13 +143,23 @@ def diff(B: int = 512, n: int = 500, n_train: int = 400, p: int = 16,
 
 def serve_trace(rate: float = 20000.0, seconds: float = 10.0, seed: int = 4,
                 n_lo: int = 20, n_hi: int = 5000, p_lo: int = 2, p_hi: int = 64,
-                max_requests: int | None = None) -> list:
+                max_requests: int | None = None, bank_rows: int | None = None) -> list:
     """Poisson arrivals (exponential gaps) at `rate` per second for `seconds`;
     each request is one fit with n log-uniform in [n_lo, n_hi] and p
     log-uniform in [p_lo, p_hi] (rounded), X ~ N(0,1), 3-sparse b_true
     ~ U(-3,3), Laplace(0,1) noise and 10% of rows shifted by +10.
+    With `bank_rows`, each request's X is a window of n consecutive rows
+    and its first p columns of one shared N(0,1) bank of bank_rows x p_hi
+    (a view, so a long trace holds the bank, not a copy per request: 10 s
+    at 20k requests/s would otherwise hold about 13 GB); its coefficients,
+    noise and outliers are its own.
     Returns a list of dicts (t_arrival, X [n,p] float32, y [n] float32)."""
     rng = np.random.default_rng(seed)
+    bank = None
+    if bank_rows is not None:
+        if bank_rows < n_hi:
+            raise ValueError("the bank must hold the longest request")
+        bank = rng.standard_normal((bank_rows, p_hi), dtype=np.float32)
     reqs = []
     t = 0.0
     while True:
@@ -160,7 +170,11 @@ def serve_trace(rate: float = 20000.0, seconds: float = 10.0, seed: int = 4,
             break
         n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
         p = int(round(np.exp(rng.uniform(np.log(p_lo), np.log(p_hi)))))
-        X = rng.standard_normal((n, p))
+        if bank is None:
+            X = rng.standard_normal((n, p))
+        else:
+            o = int(rng.integers(0, bank_rows - n + 1))
+            X = bank[o:o + n, :p]
         k = min(3, p)
         sup = rng.choice(p, k, replace=False)
         bt = np.zeros(p)
@@ -168,5 +182,6 @@ def serve_trace(rate: float = 20000.0, seconds: float = 10.0, seed: int = 4,
         y = X @ bt + rng.laplace(0.0, 1.0, n)
         out = rng.choice(n, max(1, n // 10), replace=False)
         y[out] += 10.0
-        reqs.append(dict(t=t, X=X.astype(np.float32), y=y.astype(np.float32)))
+        reqs.append(dict(t=t, X=X if bank is not None else X.astype(np.float32),
+                         y=y.astype(np.float32)))
     return reqs

@@ -1,8 +1,8 @@
 """Autotuner for the batched fit's launch shape.
 
-The fit kernel has two shapes (one warp per fit with several fits per
-thread block, or one 512-thread block per fit) and, for the one-warp shape,
-a number of fits per block bounded by shared memory; problems are taken
+The fit kernel has four shapes (a group of 32, 64 or 128 threads per fit
+with several fits per thread block, or one 512-thread block per fit) and,
+for the small groups, a number of fits per block bounded by shared memory; problems are taken
 longest first or longest and shortest alternately.  More fits per block
 hide more latency but also keep more gathered designs live in L2 at once,
 so the best choice depends on the problem mix.  `autotune` times every
@@ -60,13 +60,18 @@ def cache_key(pr: ll.Problems, L: int, opts: ll.Opts | None = None, device_name:
 
 
 def candidates(pr: ll.Problems) -> list:
-    """Launch shapes the library accepts for `pr`."""
+    """Launch shapes the library accepts for `pr`: groups of 32, 64 or 128
+    threads per fit with the most fits per block that shared memory holds
+    and down to a third of that, and one 512-thread block per fit; each in
+    both work orders."""
     out = []
-    g, fmax, mrows = ll.launch_shape(pr, ll.Launch(32, 0))
-    for order in (0, 1):
-        if pr.n_max <= mrows:
-            lo = max(1, fmax // 3)
-            out += [ll.Launch(32, f, order) for f in range(fmax, lo - 1, -1)]
+    for gt in (32, 64, 128):
+        g, fmax, mrows = ll.launch_shape(pr, ll.Launch(gt, 0))
+        if pr.n_max > mrows:
+            continue
+        lo = max(1, fmax // 3)
+        for order in (0, 1):
+            out += [ll.Launch(gt, f, order) for f in range(fmax, lo - 1, -1)]
     g, _, mrows = ll.launch_shape(pr, ll.Launch(512, 0))
     if pr.n_max <= mrows:
         out += [ll.Launch(512, 0, 0), ll.Launch(512, 0, 1)]
@@ -133,8 +138,8 @@ def autotune(pr: ll.Problems, lambdas: torch.Tensor, *, opts: ll.Opts | None = N
 
 def choose(times: dict, tie: float = 0.01):
     """The shape to use given measured seconds per shape: among shapes
-    within `tie` (relative) of the fastest, the one-warp shape with the
-    fewest fits per block, then work order 0."""
+    within `tie` (relative) of the fastest, the smallest group of threads
+    per fit, then the fewest fits per block, then work order 0."""
     best = min(times.values())
     near = [c for c, t in times.items() if t <= best * (1.0 + tie)]
-    return min(near, key=lambda c: (c.group_threads != 32, c.fits_per_block, c.work_order))
+    return min(near, key=lambda c: (c.group_threads, c.fits_per_block, c.work_order))

@@ -67,10 +67,16 @@ def test_launch_shape_is_host_only_and_consistent():
     assert g5 == 512 and m5 >= 7000
     assert ll.launch_shape(Pr(180, 7000), ll.Launch(32, 0))[2] < 7000
     assert ll.launch_shape(Pr(180, 5000))[0] == 32  # a warp still holds it
+    # two or four warps per fit: fewer fits per block (at most 512 threads),
+    # a little less room for rows than one warp (larger selection buffers)
+    for gt in (64, 128):
+        g6, f6, m6 = ll.launch_shape(Pr(32, 2000), ll.Launch(gt, 0))
+        assert g6 == gt and 1 <= f6 <= 512 // gt and f6 <= f and 8192 <= m6 <= m
     # invalid shapes
     import pytest
-    with pytest.raises(ll.LadLassoError):
-        ll.launch_shape(Pr(32, 2000), ll.Launch(64, 0))
+    for bad in (96, 256, 1024):
+        with pytest.raises(ll.LadLassoError):
+            ll.launch_shape(Pr(32, 2000), ll.Launch(bad, 0))
 
 
 def test_documented_option_defaults_match_the_library():

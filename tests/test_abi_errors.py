@@ -96,7 +96,7 @@ FIT_CASES = {
     "lambdas NULL": ({}, {"lambdas": None}, {}),
     "b_out NULL": ({}, {"b_out": None}, {}),
     "obj_out NULL": ({}, {"obj_out": None}, {}),
-    "group_threads": ({"group_threads": 64}, {}, {}),
+    "group_threads": ({"group_threads": 96}, {}, {}),
     "fits_per_block < 0": ({"fits_per_block": -1}, {}, {}),
     "work_order 2": ({"work_order": 2}, {}, {}),
     "work_order < 0": ({"work_order": -1}, {}, {}),

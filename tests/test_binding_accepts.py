@@ -33,8 +33,10 @@ def test_serving_pool_and_admission_sets_pass():
                       p=torch.from_numpy(srv.h_p[ss]), P=8, n_max=50,
                       n_rows=torch.from_numpy(srv.h_n[ss]))
     _ok(sub)
-    ll._check_out(dict(b=srv.b, obj=srv.obj, status=srv.status), srv.S, 1, 8, srv.X.device)
-    assert srv.b.numel() == srv.S * srv.P  # b_init aliases b_out at L = 1
+    # a launch takes up to K path positions per slot, warm-started from b_state
+    ll._check_out(dict(b=srv.b, obj=srv.obj, status=srv.status), srv.S, srv.K, 8, srv.X.device)
+    assert srv.K == 2 and srv.lam_step.shape == (srv.S, srv.K)
+    assert srv.b_state.numel() == srv.S * srv.P
 
 
 def test_cross_validation_sets_pass():

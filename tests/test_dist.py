@@ -8,7 +8,8 @@ import numpy as np
 import pytest
 
 from paper_2510_15649_gb300 import synth
-from paper_2510_15649_gb300.dist import (cost_shard_range, max_over_ranks, shard_batch, shard_range,
+from paper_2510_15649_gb300.dist import (cost_shard_range, cost_share, covered_once, gather_lists,
+                                         max_over_ranks, route_requests, shard_batch, shard_range,
                                          sum_over_ranks)
 
 
@@ -95,7 +96,13 @@ def _worker(rank, world, port, out):
     done[clo:chi] = 1
     dist.all_reduce(done)
     mine = float(np.sum(np.diff(part["offsets"]) * part["p"]))
-    out.put((rank, lo, hi, t, done.tolist(), mine, float(cost.sum()), total))
+    # the benchmark's strong-scaling share: the same cut with L = 16, and
+    # the coverage check over both ranks (a planted overlap fails it)
+    sb, (slo, shi) = cost_share(b, 16, rank, world)
+    assert (slo, shi) == (clo, chi) and np.array_equal(sb["y"], part["y"])
+    ok = covered_once(slo, shi, 40, dist)
+    overlap = covered_once(0, shi if rank == 0 else 40, 40, dist)
+    out.put((rank, lo, hi, t, done.tolist(), mine, float(cost.sum()), total, ok, overlap))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -120,4 +127,77 @@ def test_two_gloo_ranks_agree_on_max_time():
     assert res[0][4] == [1] * 40 and res[1][4] == [1] * 40
     assert res[0][5] + res[1][5] == res[0][6]
     assert [r[7] for r in res] == [3.0, 3.0]
+    assert [r[8] for r in res] == [True, True] and [r[9] for r in res] == [False, False]
+    assert covered_once(0, 5, 5) and not covered_once(0, 4, 5)  # no process group
     assert sum_over_ranks(2.5) == 2.5 and max_over_ranks(2.5) == 2.5  # no process group
+
+
+def test_route_requests_balances_load_in_arrival_order():
+    assert route_requests([], 3).tolist() == []
+    assert route_requests([5.0, 1.0, 1.0, 1.0], 2).tolist() == [0, 1, 1, 1]
+    assert route_requests([1.0] * 6, 3).tolist() == [0, 1, 2, 0, 1, 2]
+    rng = np.random.default_rng(0)
+    w = rng.uniform(1.0, 100.0, 500)
+    for world in (1, 2, 4, 8):
+        r = route_requests(w, world)
+        assert set(r.tolist()) <= set(range(world))
+        loads = np.bincount(r, weights=w, minlength=world)
+        # greedy least-loaded: every rank within one request of the others
+        assert loads.max() - loads.min() <= w.max()
+    with pytest.raises(ValueError):
+        route_requests([1.0, -1.0], 2)
+    with pytest.raises(ValueError):
+        route_requests([1.0], 0)
+    assert gather_lists([1, 2]) == [1, 2]  # no process group
+
+
+def _serve_worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2510_15649_gb300 import ladlasso as ll
+    from paper_2510_15649_gb300.serve import Server, serve_distributed
+    from test_serve_host import FakeLibrary
+    f = FakeLibrary()
+    for name in ("workspace", "lambda_max", "lambda_path", "fit"):
+        setattr(ll, name, getattr(f, name))
+    trace = synth.serve_trace(rate=4000.0, seconds=1.0, seed=9, n_hi=300, p_hi=8,
+                              max_requests=30)
+    srv = Server(slots=4, cap=300, P=8, L=3, device="cpu")
+    results, st = serve_distributed(srv, trace, rank, world, dist, time_scale=0.0)
+    lam_ok = all(np.isclose(r.lambdas[0], np.abs(trace[r.rid]["X"].T @ np.sign(trace[r.rid]["y"])).max(),
+                            rtol=1e-5) for r in results)
+    out.put((rank, sorted(r.rid for r in results), st.completed, st.fits, len(st.latencies),
+             st.wall, lam_ok))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_serve_one_trace_between_them():
+    import torch.multiprocessing as mp
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_serve_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    trace = synth.serve_trace(rate=4000.0, seconds=1.0, seed=9, n_hi=300, p_hi=8, max_requests=30)
+    route = route_requests([r["X"].size for r in trace], 2)
+    # each request served once, by the rank it was routed to, on its own data
+    for rank, rids, *_ in res:
+        assert rids == [i for i in range(30) if route[i] == rank]
+        assert rids
+    assert sorted(res[0][1] + res[1][1]) == list(range(30))
+    assert all(r[6] for r in res)
+    # the merged report is the same on both ranks: every request, every fit
+    for r in res:
+        assert r[2] == 30 and r[3] == 30 * 3 and r[4] == 30
+    assert res[0][5] == res[1][5]

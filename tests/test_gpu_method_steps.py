@@ -43,12 +43,21 @@ def ll():
     return ladlasso
 
 
-def _run(ll, batch, lam_np, per_thread=False, b_init=None, **kw):
+# launch shapes: threads per fit of the batched kernel, or the
+# thread-per-fit kernel (the paper's layout)
+SHAPES = ["32", "64", "128", "512", "thread"]
+
+
+def _run(ll, batch, lam_np, shape="32", b_init=None, **kw):
     import torch
     pr = ll.Problems.from_numpy(batch)
     lam = torch.as_tensor(np.asarray(lam_np, np.float32), device="cuda")
     bi = None if b_init is None else torch.as_tensor(np.asarray(b_init, np.float32), device="cuda")
-    out = ll.fit(pr, lam, b_init=bi, per_thread=per_thread, basis=True, counters=True, **kw)
+    if shape == "thread":
+        kw["per_thread"] = True
+    else:
+        kw["launch"] = ll.Launch(int(shape), 0, 0)
+    out = ll.fit(pr, lam, b_init=bi, basis=True, counters=True, **kw)
     torch.cuda.synchronize()
     return {k: v.cpu().numpy() for k, v in out.items()}
 
@@ -124,20 +133,20 @@ def _wm_problems(seed):
     return probs, np.array(lams, np.float32)[:, None]
 
 
-@pytest.mark.parametrize("per_thread", [False, True])
-def test_axis_update_is_the_weighted_median(ll, per_thread):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_axis_update_is_the_weighted_median(ll, shape):
     probs, lam = _wm_problems(61)
     batch = _stack(probs, 1)
-    out = _run(ll, batch, lam, per_thread,
-               opts=ll.default_opts(chop=0, polish=0, max_sweeps=1))
+    out = _run(ll, batch, lam, shape, opts=ll.default_opts(chop=0, polish=0, max_sweeps=1))
+    per_thread = shape == "thread"
     o = oracle.default_opts(chop=0, polish=0, max_sweeps=1)
     decisive = 0
     for q, (Xq, yq) in enumerate(probs):
         X, y = Xq.astype(np.float64), yq.astype(np.float64)
         lq = float(lam[q, 0])
         ref = oracle.fit_path(X, y, [lq], opts=o)
-        # the warp kernel sums each lane's rows in sequence, then across
-        # lanes; the thread kernel sums all rows in sequence
+        # the batched kernel sums each lane's rows in sequence, then across
+        # lanes and warps; the thread kernel sums all rows in sequence
         terms = len(y) + 1 if per_thread else len(y) / 32 + 16
         med, dec, half = _median_decision(X[:, 0], y, lq, terms)
         bg, bo = float(out["b"][q, 0, 0]), float(ref["b"][0][0])
@@ -188,15 +197,15 @@ def _p2_problems(seed, count=10):
 
 
 @pytest.mark.parametrize("sections", [3, 4])
-@pytest.mark.parametrize("per_thread", [False, True])
-def test_two_coordinate_chop_reaches_the_brute_force_optimum(ll, sections, per_thread):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_two_coordinate_chop_reaches_the_brute_force_optimum(ll, sections, shape):
     probs = _p2_problems(67 + sections)
     batch = _stack(probs, 2)
     lam = np.array([[0.05 * oracle.lambda_max(X.astype(np.float64), y.astype(np.float64))]
                     for X, y in probs], np.float32)
     opts = ll.default_opts(polish=0, chop_sections=sections, chop_tol=1e-6,
                            chop_max_probes=240, chop_max_extend=60)
-    out = _run(ll, batch, lam, per_thread, opts=opts)
+    out = _run(ll, batch, lam, shape, opts=opts)
     ran = 0
     for q, (Xq, yq) in enumerate(probs):
         X, y = Xq.astype(np.float64), yq.astype(np.float64)
@@ -211,15 +220,15 @@ def test_two_coordinate_chop_reaches_the_brute_force_optimum(ll, sections, per_t
 
 # ------------------------------------------------------------------ (c)
 
-@pytest.mark.parametrize("per_thread", [False, True])
-def test_chop_in_exact_arithmetic_matches_the_oracle(ll, per_thread):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_chop_in_exact_arithmetic_matches_the_oracle(ll, shape):
     probs, lam = exact_problems(73)
     batch = _stack(probs, 8)
     # multipliers of these +-1 bases are rationals of denominator det(B)
     # (at least 1/4096 away from their caps unless exactly at them), so a
     # float32 tolerance of 1e-6 and the oracle's 1e-10 judge them alike
     kw = EXACT_CHOP_OPTS
-    out = _run(ll, batch, lam, per_thread, opts=ll.default_opts(tol_opt=1e-6, **kw))
+    out = _run(ll, batch, lam, shape, opts=ll.default_opts(tol_opt=1e-6, **kw))
     o = oracle.default_opts(tol_move=1e-6, **kw)
     chopped = 0
     for q, (Xq, yq) in enumerate(probs):
@@ -250,8 +259,8 @@ def _axis_gain(X, y, b, lam):
     return best, f0
 
 
-@pytest.mark.parametrize("per_thread", [False, True])
-def test_chop_only_fits_on_the_batched_recipe(ll, per_thread):
+@pytest.mark.parametrize("shape", ["32", "64", "128", "thread"])
+def test_chop_only_fits_on_the_batched_recipe(ll, shape):
     """General float32 data: descent from the same start stops at points
     that float32 rounding moves (in FP64, perturbing the inputs by one
     float32 rounding already changes the stopping point of about half of
@@ -264,7 +273,7 @@ def test_chop_only_fits_on_the_batched_recipe(ll, per_thread):
     lm = np.array([oracle.lambda_max(*oracle.problem(batch, q)) for q in range(B)])
     lam = (lm[:, None] * 0.3 ** np.arange(L)[None, :]).astype(np.float32)
     gopts = ll.default_opts(polish=0)
-    out = _run(ll, batch, lam, per_thread, opts=gopts)
+    out = _run(ll, batch, lam, shape, opts=gopts)
     o = oracle.default_opts(polish=0, tol_move=float(gopts.tol_move))
     same_probes = close = total = chopped = 0
     for q in range(B):

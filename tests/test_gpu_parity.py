@@ -61,6 +61,18 @@ def test_batched_small_parity(ll, per_thread):
     assert np.all((out["status"] & 1) == 0)
 
 
+@pytest.mark.parametrize("group", [64, 128, 512])
+def test_batched_small_parity_multiwarp(ll, group):
+    # the same problems with 2, 4 or 16 warps sharing each fit
+    batch = synth.batched_like(48, 20, 700, 1, 12, R=800, P=12, seed=11)
+    lam = _oracle_lams(batch, 5, 1e-3)
+    out = _run(ll, batch, lam, launch=ll.Launch(group, 0, 0))
+    res = compare(batch, lam, out["b"], out["obj"], out["status"])
+    assert not res["bad"], res["bad"][:10]
+    assert np.all((out["status"] & 1) == 0)
+    assert res["support_checked"] >= 0.5 * res["checked"], res
+
+
 def test_lambda_max_and_path(ll):
     import torch
     batch = synth.batched_like(40, 5, 500, 1, 16, R=600, P=16, seed=3)

@@ -60,3 +60,30 @@ def test_headline_workload_sampled_parity(ll):
     assert res["support_checked"] >= 0.75 * res["checked"], res
     print(f"support-checked {res['support_checked']} of {res['checked']} fits, "
           f"objective only {res['objective_only']}")
+
+
+@pytest.mark.parametrize("group", [64, 128])
+def test_headline_workload_sampled_parity_multiwarp(ll, group):
+    """The same workload with 2 or 4 warps sharing each fit: its own sums
+    (warp order), so compared with the oracle on its own; fits per block and
+    work order change nothing, bit for bit."""
+    import torch
+    batch = synth.batched()
+    pr = ll.Problems.from_numpy(batch)
+    lam = ll.lambda_path(ll.lambda_max(pr), L, 1e-3)
+    _, fmax, _ = ll.launch_shape(pr, ll.Launch(group, 0))
+    runs = []
+    for launch in (ll.Launch(group, fmax, 0), ll.Launch(group, max(1, fmax // 2), 1)):
+        out = ll.fit(pr, lam, launch=launch)
+        torch.cuda.synchronize()
+        runs.append({k: v.cpu().numpy() for k, v in out.items()})
+    for k in ("b", "obj", "status"):
+        assert np.array_equal(runs[0][k], runs[1][k]), k
+    ref = runs[0]
+    assert not np.any(ref["status"] & 2)
+    assert np.mean((ref["status"] & 1) == 0) >= 0.999
+    qs = sample_problems(batch)
+    res = compare_parallel(batch, lam.cpu().numpy(), ref["b"], ref["obj"], ref["status"], qs)
+    assert res["checked"] == len(qs) * L
+    assert not res["bad"], res["bad"][:10]
+    assert res["support_checked"] >= 0.75 * res["checked"], res

@@ -48,6 +48,7 @@ class FakeLibrary:
         self.calls = 0
         self.fail_at_step = fail_at_step
         self.max_used = 0
+        self.positions = []  # per launch: positions each active slot took
 
     def workspace(self, pr, L=1):
         import torch
@@ -73,27 +74,33 @@ class FakeLibrary:
         t = np.arange(L) / max(1, L - 1)
         return torch.from_numpy((lmax.numpy()[:, None] * ratio ** t).astype(np.float32))
 
-    def fit(self, pr, lambdas, *, b_init=None, opts=None, ws=None, out=None, **kw):
+    def fit(self, pr, lambdas, *, b_init=None, opts=None, ws=None, out=None, launch=None, **kw):
         from paper_2510_15649_gb300 import ladlasso as ll
         self.calls += 1
         if self.calls == self.fail_at_step:
             raise ll.LadLassoError("injected failure")
-        lam = lambdas.numpy()[:, 0]
+        lam = lambdas.numpy()  # [S, K]: a slot's positions first, NaN after
         nr, p = pr.n_rows.numpy(), pr.p.numpy()
-        active = np.nonzero(np.isfinite(lam))[0]
+        ok = np.isfinite(lam)
+        active = np.nonzero(ok[:, 0])[0]
+        self.positions.append(ok.sum(axis=1)[active].tolist())
+        # valid positions come first, then NaN
+        assert np.all(ok[:, 1:] <= ok[:, :-1]), "a valid position after a NaN one"
         assert np.all(nr[active] > 0), "a slot with a lambda holds no rows"
         # the server's contract: idle slots are passed with NaN and 0 rows
-        assert np.all(nr[~np.isfinite(lam)] == 0), "an idle slot still passes rows"
+        assert np.all(nr[~ok[:, 0]] == 0), "an idle slot still passes rows"
         self.max_used = max(self.max_used, int((nr[active] * p[active]).sum()))
-        b0 = b_init.numpy()[:, 0].copy()
+        bcur = b_init.numpy().copy()  # [S, P]: each position warm-starts the next
         b, obj, st = out["b"].numpy(), out["obj"].numpy(), out["status"].numpy()
-        for q in range(len(lam)):
-            if q in active:
-                b[q, 0] = 0.0
-                b[q, 0, :p[q]] = b0[q, :p[q]] + 1.0
-                obj[q, 0], st[q, 0] = lam[q], 0
-            else:
-                b[q, 0], obj[q, 0], st[q, 0] = 0.0, 0.0, 2
+        for q in range(lam.shape[0]):
+            for l in range(lam.shape[1]):
+                b[q, l] = 0.0
+                if ok[q, l]:
+                    bcur[q, :p[q]] += 1.0
+                    b[q, l, :p[q]] = bcur[q, :p[q]]
+                    obj[q, l], st[q, l] = lam[q, l], 0
+                else:
+                    obj[q, l], st[q, l] = 0.0, 2
         return out
 
 
@@ -138,6 +145,32 @@ def test_every_request_is_fitted_on_its_own_data_and_warm_started(fake):
         assert np.array_equal(r.obj, r.lambdas) and np.all(r.status == 0)
         assert r.t_done >= r.t_arrival
     assert f.calls == st.steps
+
+
+def test_small_requests_take_several_positions_per_launch(fake):
+    from paper_2510_15649_gb300.serve import Server
+    f = fake()
+    rng = np.random.default_rng(4)
+    # one long request and short ones arriving together: the short ones
+    # finish their 4-position paths in one launch, the long one takes one
+    # position per launch; every warm start still carries through
+    mk = lambda n, p: dict(t=0.0, X=rng.standard_normal((n, p)).astype(np.float32),  # noqa: E731
+                           y=rng.standard_normal(n).astype(np.float32))
+    trace = [mk(280, 8)] + [mk(20, 2) for _ in range(3)]
+    srv = Server(slots=4, cap=300, P=8, L=4, device="cpu")
+    results, st = srv.run(trace, time_scale=0.0)
+    assert st.completed == 4 and st.fits == 16 and st.steps == 4
+    assert f.positions[0] == [1, 4, 4, 4] or sorted(f.positions[0]) == [1, 4, 4, 4]
+    assert all(x == [1] for x in f.positions[1:])
+    for r in results:
+        for l in range(4):
+            assert np.all(r.b[l] == l + 1.0)
+    # one position per launch when asked
+    f2 = fake()
+    srv = Server(slots=4, cap=300, P=8, L=4, device="cpu", positions_per_step=1)
+    results, st = srv.run(trace, time_scale=0.0)
+    assert st.steps == 4 and all(set(x) == {1} for x in f2.positions)
+    assert all(np.all(r.b[l] == l + 1.0) for r in results for l in range(4))
 
 
 def test_memory_budget_bounds_the_active_work(fake):

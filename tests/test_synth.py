@@ -1,6 +1,7 @@
 """The seeded input recipes: sizes, ranges, structure and determinism of
 every workload generator (tiny, batched, large, diff, serving trace)."""
 import numpy as np
+import pytest
 
 from paper_2510_15649_gb300 import synth
 
@@ -90,3 +91,18 @@ def test_serving_trace_recipe():
     again = synth.serve_trace(rate=20000.0, seconds=0.25, seed=4)
     assert len(again) == len(tr) and np.array_equal(again[7]["y"], tr[7]["y"])
     assert len(synth.serve_trace(rate=20000.0, seconds=0.25, seed=4, max_requests=10)) == 10
+    # a shared row bank: views of one N(0,1) matrix, the same size mix,
+    # each request's own targets (its coefficients, noise and outliers)
+    bk = synth.serve_trace(rate=20000.0, seconds=0.05, seed=4, bank_rows=20000)
+    nb = np.array([r["X"].shape[0] for r in bk])
+    assert abs(len(bk) - 1000) < 130 and nb.min() >= 20 and nb.max() <= 5000
+    base = bk[0]["X"].base
+    assert base is not None and all(r["X"].base is base for r in bk)
+    assert base.shape == (20000, 64) and abs(float(base.std()) - 1.0) < 0.01
+    for r in bk[:20]:
+        X = r["X"].astype(np.float64)
+        res = r["y"] - X @ np.linalg.lstsq(X, r["y"], rcond=None)[0]
+        assert r["X"].dtype == np.float32 and r["y"].shape == (X.shape[0],)
+        assert np.abs(res).max() > 0  # noise on every request
+    with pytest.raises(ValueError):
+        synth.serve_trace(rate=100.0, seconds=0.1, seed=1, bank_rows=100)

@@ -9,13 +9,15 @@ class Pr:  # the fields candidates() reads
         self.P, self.n_max = P, n_max
 
 
-def test_candidates_cover_both_shapes_and_orders_when_both_fit():
+def test_candidates_cover_every_shape_and_order_when_all_fit():
     c = tune.candidates(Pr(32, 2000))
-    warp = [x for x in c if x.group_threads == 32]
+    for gt in (32, 64, 128):
+        grp = [x for x in c if x.group_threads == gt]
+        _, fmax, _ = ll.launch_shape(Pr(32, 2000), ll.Launch(gt, 0))
+        assert fmax >= 1 and fmax * gt <= 512
+        assert {x.fits_per_block for x in grp} == set(range(max(1, fmax // 3), fmax + 1))
+        assert {x.work_order for x in grp} == {0, 1}
     block = [x for x in c if x.group_threads == 512]
-    _, fmax, _ = ll.launch_shape(Pr(32, 2000))
-    assert {x.fits_per_block for x in warp} == set(range(max(1, fmax // 3), fmax + 1))
-    assert {x.work_order for x in warp} == {0, 1}
     assert block == [ll.Launch(512, 0, 0), ll.Launch(512, 0, 1)]
     assert len(set(c)) == len(c)
 
@@ -77,6 +79,12 @@ def test_choice_prefers_fewer_fits_within_the_tie():
     # the one-warp shape before the block shape at equal time
     assert tune.choose({blk: 1.0, W(6): 1.0}) == W(6)
     assert tune.choose({blk: 1.0, W(6): 1.5}) == blk
+    # smaller groups first within the tie, then fewer fits per block
+    G2 = ll.Launch(64, 6, 0)
+    G4 = ll.Launch(128, 4, 0)
+    assert tune.choose({G4: 1.0, G2: 1.005, W(6): 1.5}) == G2
+    assert tune.choose({G4: 1.0, G2: 1.2}) == G4
+    assert tune.choose({G2: 1.0, W(6): 1.009}) == W(6)
     # a wider tie admits slower shapes
     assert tune.choose({W(6): 1.0, W(2): 1.04}, tie=0.05) == W(2)
 
