@@ -68,6 +68,7 @@ constexpr int kMaxPasses = 64; // cap on fused passes per 1-D step
 constexpr int kSubCap = 128;   // block path: selection sub-buffer per warp
 constexpr int kBlockG = 512;   // block path: threads per fit
 constexpr int kHist = 32;               // polish: bases remembered for cycle detection
+constexpr int kReanchor = 8;            // polish: pivots between residuals from the design
 constexpr int kChgW = 256;              // block polish: changed rows per warp before a full recompute
 constexpr float kStallTolFactor = 50.f; // cycling vertex accepted when violations are below this x tol
 
@@ -1880,11 +1881,14 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
   if (warp == 0) basis_seen(s, 0);  // the starting basis
   gsync<G>();
   nh = 1;
+  int fresh = 1;  // r was recomputed from the design at this vertex
   for (;;) {
     snap_g<G>(s);
     gsync<G>();
     if (!s.flag) { exit_code = 4; break; }  // singular basis: give up (status MAX_ITERS)
-    recompute_r<G>(s);
+    // r: moved along the edge by the last step (below), recomputed from the
+    // design at the first vertex and every kReanchor pivots
+    if (it % kReanchor == 0) { recompute_r<G>(s); fresh = 1; }
     for (int w = tid; w < s.maskw; w += G) s.mask[w] = 0u;
     gsync<G>();
     if (tid == 0)
@@ -1936,6 +1940,10 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     const float ts = s.zstar;
     const int own = s.owner;
     if (own == kNone) { exit_code = 5; break; }  // flat along the edge (cannot happen when F decreases)
+    // residual along the edge: r_i -= t x_i . d (the edge products are in
+    // the line search's factor; zero on the basis rows that stay)
+    axpy_r<G>(s, s.colp, ts);
+    fresh = 0;
     if (warp == 0) {
       for (int c = lane; c < p; c += 32) s.bv[c] += ts * s.dv[c];
       __syncwarp();
@@ -1961,6 +1969,8 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     ++it;
   }
   gsync<G>();
+  if (!fresh) recompute_r<G>(s);  // r exact at the vertex the polish ends on
+  gsync<G>();
   if (tid == 0) s.pexit = exit_code;
   gsync<G>();
   return it;
@@ -1973,14 +1983,25 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
 template <int G>
 __device__ __noinline__ int stall_test(St& s, int* nonu) {
   for (int c = gtid<G>(); c < s.p; c += G) s.bbest[c] = s.bv[c];
+  if (kSmemCols<G>) {
+    // the residual is kept in the second column buffer (idle until the
+    // descent resumes) instead of being recomputed from the design
+    cp_async_wait_all();
+    gsync<G>();
+    for (int i = gtid<G>(); i < s.n; i += G) s.cb[1][i] = s.rr[i];
+  }
   if (gwarp<G>() == 0) build_basis(s);
   gsync<G>();
   int is_opt = 0;
   polish<G>(s, 0, &is_opt, nonu);
   if (!is_opt) {
     for (int c = gtid<G>(); c < s.p; c += G) s.bv[c] = s.bbest[c];
-    gsync<G>();
-    recompute_r<G>(s);
+    if (kSmemCols<G>) {
+      for (int i = gtid<G>(); i < s.n; i += G) s.rr[i] = s.cb[1][i];
+    } else {
+      gsync<G>();
+      recompute_r<G>(s);
+    }
     gsync<G>();
   }
   return is_opt;
