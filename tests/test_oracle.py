@@ -110,6 +110,36 @@ def test_dual_lp_value_equals_the_method_optimum():
             assert rel(info["dual"], -dual.fun) < 1e-8
 
 
+def test_method_optimum_equals_highs_dual_at_workload_sizes():
+    # the oracle's method at the sizes the GPU runs (the batched workload's
+    # problems across its range of n, up to 2000 x 32; the large recipe at
+    # 1500 x 64; the differentiation recipe's 400 x 16 training rows) against
+    # the bounded dual LP (Section 3.1, lambda on |b|_1) solved by scipy's
+    # HiGHS -- an exact solver that shares nothing with the method
+    linprog = pytest.importorskip("scipy.optimize").linprog
+    from paper_2510_15649_gb300 import synth
+    cases = []
+    b = synth.batched(B=4096, seed=1)
+    n = np.diff(b["offsets"])
+    for q in np.argsort(n, kind="stable")[np.linspace(0, 4095, 6).round().astype(int)]:
+        cases.append(oracle.problem(b, int(q)))
+    big = synth.large(B=1, n=1500, p=64, seed=3)
+    cases.append((big["X"].astype(np.float64), big["y"].astype(np.float64)))
+    d = synth.diff(B=2, seed=3)["train"]
+    cases.append(oracle.problem(d, 1))
+    for X, y in cases:
+        p = X.shape[1]
+        lm = oracle.lambda_max(X, y)
+        lams = lm * np.array([0.5, 0.1, 0.01, 0.001])
+        r = oracle.fit_path(X, y, lams)
+        A = np.vstack([X.T, -X.T])
+        for l, lam in enumerate(lams):
+            dual = linprog(-y, A_ub=A, b_ub=lam * np.ones(2 * p), bounds=(-1, 1), method="highs")
+            assert dual.status == 0
+            assert rel(r["f"][l], -dual.fun) < 1e-9, (X.shape, l, r["f"][l], -dual.fun)
+            assert r["status"][l] & 1 == 0
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_random_tiny_brute_equals_simplex_equals_method(seed):
     rng = np.random.default_rng(100 + seed)
