@@ -146,7 +146,9 @@ void ladlasso_default_opts(ladlasso_opts* o);
  *            rounded up, so that a small problem set still spreads over
  *            every SM); results do not depend on it.
  * work_order order in which the fits take problems: 0 = longest first
- *            (n * p), 1 = longest and shortest alternately (a smaller L2
+ *            (estimated cost p * (n + 1024): each 1-D step has a fixed
+ *            part worth about a thousand rows), 1 = longest and shortest
+ *            alternately (a smaller L2
  *            working set of resident designs); any other value is
  *            LADLASSO_ERR_INVALID.  Results do not depend on it.
  *            The three are chosen by the autotuner of the Python binding;

@@ -54,7 +54,7 @@ struct FitArgs {
   int32_t* counters;
   float* Xg;        // workspace: gathered column-major designs
   int* queue;       // workspace: work counter (queue[0]) and offsets flag (queue[1])
-  int* order;       // workspace: problems in decreasing estimated cost (block path)
+  int* order;       // workspace: problems in decreasing estimated cost
   unsigned char* scratch;  // workspace: per-fit scratch (thread-per-fit kernel)
   int B, P, L, n_max;
   int64_t ldX, rows_X, total_rows;

@@ -22,7 +22,7 @@ def shard_range(B: int, rank: int, world: int) -> tuple:
 
 def cost_shard_range(cost, rank: int, world: int) -> tuple:
     """Contiguous share [lo, hi) of the problems for `rank` of `world`,
-    balanced by per-problem cost (e.g. n * p * L, the work a fit does
+    balanced by per-problem cost (e.g. problem_cost, the work a fit does
     along its path): rank r's share ends at the prefix whose running cost
     is nearest to (r + 1) / world of the total, so every boundary is within
     half a problem's cost of its target and every rank's cost within one
@@ -74,14 +74,24 @@ def shard_batch(batch: dict, lo: int, hi: int) -> dict:
     return out
 
 
+STEP_ROWS = 1024  # a 1-D step's fixed work (window sums, selection), in rows
+
+
+def problem_cost(batch: dict, L: int) -> "np.ndarray":
+    """Estimated work of each problem's fit along an L-point path,
+    p * (n + STEP_ROWS) * L: about p 1-D steps per sweep, each a pass over
+    the n rows plus a fixed part worth about a thousand rows (the estimate
+    the fit kernels' longest-first work order uses)."""
+    import numpy as np
+    n = np.diff(np.asarray(batch["offsets"], np.int64)).astype(np.float64)
+    return np.asarray(batch["p"], np.float64) * (n + STEP_ROWS) * L
+
+
 def cost_share(batch: dict, L: int, rank: int, world: int) -> tuple:
     """This rank's share of one batch for strong scaling: contiguous
-    problems balanced by n * p * L (cost_shard_range), cut out with
+    problems balanced by problem_cost (cost_shard_range), cut out with
     shard_batch.  Returns (the share as a batch, (lo, hi))."""
-    import numpy as np
-    cost = np.diff(np.asarray(batch["offsets"], np.int64)).astype(np.float64) \
-        * np.asarray(batch["p"], np.float64) * L
-    lo, hi = cost_shard_range(cost, rank, world)
+    lo, hi = cost_shard_range(problem_cost(batch, L), rank, world)
     return shard_batch(batch, lo, hi), (lo, hi)
 
 

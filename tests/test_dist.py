@@ -9,6 +9,7 @@ import pytest
 
 from paper_2510_15649_gb300 import synth
 from paper_2510_15649_gb300.dist import (cost_shard_range, cost_share, covered_once, gather_lists,
+                                         problem_cost,
                                          max_over_ranks, route_requests, shard_batch, shard_range,
                                          sum_over_ranks)
 
@@ -24,6 +25,12 @@ def test_shards_cover_every_problem_once():
             assert seen == list(range(B))
     with pytest.raises(ValueError):
         shard_range(4, 2, 2)
+
+
+def test_problem_cost_is_steps_times_rows_plus_fixed_part():
+    b = dict(offsets=np.array([0, 10, 10, 2010]), p=np.array([3, 1, 32]))
+    assert problem_cost(b, 1).tolist() == [3 * 1034.0, 1024.0, 32 * 3024.0]
+    assert problem_cost(b, 16).tolist() == [16 * 3 * 1034.0, 16 * 1024.0, 16 * 32 * 3024.0]
 
 
 def _ranges(cost, world):
@@ -89,13 +96,13 @@ def _worker(rank, world, port, out):
     # cost-balanced shares of one batch: every problem fitted exactly once
     import torch
     b = synth.batched_like(40, 5, 200, 2, 8, R=250, P=8, seed=7)
-    cost = np.diff(b["offsets"]) * b["p"]
+    cost = problem_cost(b, 1)
     clo, chi = cost_shard_range(cost, rank, world)
     part = shard_batch(b, clo, chi)
     done = torch.zeros(40, dtype=torch.int64)
     done[clo:chi] = 1
     dist.all_reduce(done)
-    mine = float(np.sum(np.diff(part["offsets"]) * part["p"]))
+    mine = float(problem_cost(part, 1).sum())
     # the benchmark's strong-scaling share: the same cut with L = 16, and
     # the coverage check over both ranks (a planted overlap fails it)
     sb, (slo, shi) = cost_share(b, 16, rank, world)
