@@ -62,7 +62,12 @@ constexpr float kDlf = LL_DLF;    // axis window half-width, times the axis' las
 #ifndef LL_ROWU
 #define LL_ROWU 8
 #endif
+#ifndef LL_FINU
+#define LL_FINU 4
+#endif
 constexpr int kU = LL_KU;      // elements per thread per compaction chunk
+constexpr int kFinU = LL_FINU; // buffered keys per lane in the selection's finish
+constexpr int kFinCap = 32 * kFinU;  // the finish takes at most this many keys
 constexpr int kBufCap = 256;   // selection buffer of the one-warp path
 constexpr int kMaxPasses = 64; // cap on fused passes per 1-D step
 constexpr int kSubCap = 128;   // block path: selection sub-buffer per warp
@@ -396,7 +401,10 @@ __device__ __noinline__ float min_key_above(St& s, float z) {
 // smallest key above the buffer's (for exact halves).  Each level brackets
 // the target with 32 samples, classifies the elements into (<lo, ==lo,
 // (lo,hi), ==hi, >hi) with fixed-order sums and compacts the part holding
-// the target in place; <= 32 elements are sorted by one warp.
+// the target in place.  At most kFinCap elements are finished by one warp,
+// kFinU per lane: each element's cumulative weight is summed over the
+// buffer in buffer order (a level costs more than this quadratic finish
+// at these sizes).
 template <int G>
 __device__ __noinline__ void select_buf(St& s, int m0, float cur, int first0, float acc0,
                                         float half0, int above_ok0, float wbuf) {
@@ -412,7 +420,7 @@ __device__ __noinline__ void select_buf(St& s, int m0, float cur, int first0, fl
   for (;;) {
     const int m = s.m;
     const int first = s.first;
-    if (m <= 32) break;
+    if (m <= kFinCap) break;
     if (warp == 0) {
       int e = (int)(((int64_t)lane * m) / 32);
       s.sampk[lane] = s.ck[e];
@@ -462,8 +470,14 @@ __device__ __noinline__ void select_buf(St& s, int m0, float cur, int first0, fl
         if (!in) bk[u] = NAN;  // marks "not kept"
         cnt += in;
       }
-      int total;
-      int pos = base + gscan<G>(s, cnt, total);
+      int total, pos;
+      if constexpr (G == 32 && kU == 1) {  // one warp, one element a lane
+        const unsigned msk = __ballot_sync(0xffffffffu, cnt != 0);
+        total = __popc(msk);
+        pos = base + __popc(msk & ((1u << lane) - 1u));
+      } else {
+        pos = base + gscan<G>(s, cnt, total);
+      }
       __syncwarp();
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
@@ -476,38 +490,61 @@ __device__ __noinline__ void select_buf(St& s, int m0, float cur, int first0, fl
     gsync<G>();
   }
   if (!s.flag && warp == 0) {
-    // at most 32 candidates, one per lane.  For each, the weight of all
-    // candidates with key <= its key (one pass over the candidates, read as
-    // shared-memory broadcasts); the target key is the smallest key whose
-    // cumulative weight (plus acc) reaches half.
+    // at most kFinCap candidates, kFinU per lane.  For each, the weight of
+    // all candidates with key <= its key (one pass over the candidates in
+    // buffer order, read as shared-memory broadcasts); the target key is
+    // the smallest key whose cumulative weight (plus acc) reaches half.
     const int m = s.m;
     const int first = s.first;
     const float* __restrict__ ck = s.ck;
     const float* __restrict__ cw = s.cw;
-    const bool have = lane < m;
-    const float k = have ? ck[lane] : kInf;
-    const float w = have ? cw[lane] : 0.f;
-    const int id = have ? ((first && lane < n) ? lane : s.cid[lane]) : INT32_MAX;
-    float cle = 0.f;
+    float k[kFinU], w[kFinU], cle[kFinU];
+    int id[kFinU];
+#pragma unroll
+    for (int u = 0; u < kFinU; ++u) {
+      const int e = u * 32 + lane;
+      const bool have = e < m;
+      k[u] = have ? ck[e] : kInf;
+      w[u] = have ? cw[e] : 0.f;
+      id[u] = have ? ((first && e < n) ? e : s.cid[e]) : INT32_MAX;
+      cle[u] = 0.f;
+    }
     for (int j = 0; j < m; ++j) {
-      const float kj = ck[j];
-      if (kj <= k) cle += cw[j];
+      const float kj = ck[j], wj = cw[j];
+#pragma unroll
+      for (int u = 0; u < kFinU; ++u)
+        if (kj <= k[u]) cle[u] += wj;
     }
     const float acc = s.acc, half = s.half;
-    const bool cand = have && acc + cle >= half;
-    float z = warp_min(cand ? k : kInf);
+    float zc = kInf;
+#pragma unroll
+    for (int u = 0; u < kFinU; ++u)
+      if (u * 32 + lane < m && acc + cle[u] >= half) zc = fminf(zc, k[u]);
+    float z = warp_min(zc);
     if (!(z < kInf)) {
       // rounding left every cumulative below half: the largest positive-weight key
-      float zmax = have && w > 0.f ? k : -kInf;
+      float zmax = -kInf;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
-      z = zmax;
+      for (int u = 0; u < kFinU; ++u)
+        if (u * 32 + lane < m && w[u] > 0.f) zmax = fmaxf(zmax, k[u]);
+      z = warp_max(zmax);
     }
-    int own = have && k == z && w > 0.f ? id : INT32_MAX;
+    int own = INT32_MAX;
+    float cz = -1.f, nx = kInf;
+#pragma unroll
+    for (int u = 0; u < kFinU; ++u) {
+      if (u * 32 + lane >= m) continue;
+      if (k[u] == z) {
+        if (w[u] > 0.f) own = min(own, id[u]);
+        cz = cle[u];  // the same for every key equal to z
+      } else if (k[u] > z) {
+        nx = fminf(nx, k[u]);
+      }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) own = min(own, __shfl_xor_sync(0xffffffffu, own, o));
-    const float cum_g = acc + __shfl_sync(0xffffffffu, cle, __ffs(__ballot_sync(0xffffffffu, have && k == z)) - 1);
-    const float next_in = warp_min(have && k > z ? k : kInf);
+    const float cum_g = acc + warp_max(cz);
+    const float next_in = warp_min(nx);
     if (lane == 0) {
       const float next = fminf(next_in, s.above);
       if (m > 0 && z < kInf && z > -kInf) finalize(s, z, own == INT32_MAX ? kNone : own, cum_g, next, cur);
@@ -648,7 +685,12 @@ __device__ __forceinline__ void smem_rows(uint32_t col_s, uint32_t rr_s, float p
   }
 }
 
-__device__ __noinline__ void fused_pass(St& s, float lo, float hi) {
+// (one warp) one pass over the rows and the special breakpoints against
+// the window [lo, hi]; every lane gets the weight below lo (wl), at or
+// below hi (wle), the total (wt) and the count of keys inside (cnt), the
+// first kBufCap of which are in the buffer.
+__device__ __noinline__ void fused_pass(St& s, float lo, float hi, float& wl_o, float& wle_o,
+                                        float& wt_o, int& cnt_o) {
   const int lane = lane_id();
   const int n = s.n, nspec = s.nspec;
   float* __restrict__ bk = s.ck;
@@ -668,11 +710,10 @@ __device__ __noinline__ void fused_pass(St& s, float lo, float hi) {
     classify_one(bk, bw, bi, v ? sk[e] : kInf, v ? sw[e] : 0.f, v ? sid[e] : 0, v, lo, hi, al,
                  ale, at, base, kBufCap);
   }
-  al = warp_sum(al);
-  ale = warp_sum(ale);
-  at = warp_sum(at);
-  __syncwarp();
-  if (lane == 0) { s.p_wl = al; s.p_wi = ale; s.p_wt = at; s.p_cnt = base; }
+  wl_o = warp_sum(al);
+  wle_o = warp_sum(ale);
+  wt_o = warp_sum(at);
+  cnt_o = base;  // uniform: every lane counted every ballot
   __syncwarp();
 }
 
@@ -739,10 +780,10 @@ __device__ __noinline__ void select_fused(St& s, float cur, bool prior, float lo
   float half = -1.f;
   if (lane == 0) s.selects++;
   for (int it = 0; it < kMaxPasses; ++it) {
-    fused_pass(s, lo, hi);
+    float wl, wle, wt;
+    int cnt;
+    fused_pass(s, lo, hi, wl, wle, wt, cnt);
     if (lane == 0) s.passes++;
-    const float wl = s.p_wl, wle = s.p_wi, wt = s.p_wt;
-    const int cnt = s.p_cnt;
     if (half < 0.f) {
       if (!(wt > 0.f)) {
         __syncwarp();
@@ -1487,6 +1528,63 @@ __device__ __noinline__ void recompute_r(St& s) {
   }
 }
 
+// (all G threads) r = y - X b at the vertex of the current basis, with
+// every sign exact.  A float32 residual can put a row whose residual lies
+// within float32 rounding of zero on the wrong side, and that row's sign
+// then enters the column sums, so the multiplier test can pass at a vertex
+// that is not optimal.  Each r_i is formed in float32 together with the
+// magnitude S_i = |y_i| + sum_c |x_ic b_c| of its terms; the rounding error
+// of that sum, and the error of the float vertex itself, stay below
+// 2^-14 S_i for p <= 256.  Only rows inside that band (a few per thousand)
+// are formed again in FP64, at the vertex b + e, where e is one correction
+// solved with the basis factors from the basis equations' residual formed
+// in FP64; a residual within FP64 resolution of zero (2^-40 of the
+// magnitude of its terms) is set to 0 (the row lies on its hyperplane).
+// FP64 is kept to these few rows: its throughput on this part is a small
+// fraction of float32's.  Needs the current basis factored (snap) and s.bv
+// its float vertex.
+template <int G>
+__device__ __noinline__ void exact_residual(St& s) {
+  constexpr int W = G / 32;
+  const int lane = lane_id(), warp = gwarp<G>(), tid = gtid<G>(), p = s.p, n = s.n;
+  gsync<G>();
+  for (int e = warp; e < p; e += W) {  // basis equation e: x_cd . b = y_cd, or b_j = const
+    const int cd = s.code[e];
+    double acc = 0.0;
+    if (cd >= 0) {
+      for (int c = lane; c < p; c += 32) acc += (double)xval(s, c, cd) * (double)s.bv[c];
+      acc = warp_sum_d(acc);
+      acc = (double)s.yq[cd] - acc;
+    }
+    if (lane == 0) s.rv[e] = (float)acc;  // coordinate equations hold exactly (snap)
+  }
+  gsync<G>();
+  if (warp == 0) lu_solve(s, s.rv);
+  gsync<G>();
+  const float* __restrict__ bv = s.bv;
+  const float* __restrict__ ev = s.rv;
+  for (int i = tid; i < n; i += G) {
+    const float yi = s.yq[i];
+    float acc = yi, mag = fabsf(yi);
+    for (int c = 0; c < p; ++c) {
+      const float t = xval(s, c, i) * bv[c];
+      acc -= t;
+      mag += fabsf(t);
+    }
+    if (fabsf(acc) <= 0x1p-14f * mag) {  // sign within float32 rounding
+      double a = (double)yi, m = fabs(a);
+      for (int c = 0; c < p; ++c) {
+        const double t = (double)xval(s, c, i) * ((double)bv[c] + (double)ev[c]);
+        a -= t;
+        m += fabs(t);
+      }
+      acc = fabs(a) <= 0x1p-40 * m ? 0.f : (float)a;
+    }
+    s.rr[i] = acc;
+  }
+  gsync<G>();
+}
+
 // r -= d * column (global or shared), loads batched kRowU<G> per thread.
 template <int G>
 __device__ __noinline__ void axpy_r(St& s, const float* __restrict__ col, float d) {
@@ -1884,13 +1982,14 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
   gsync<G>();
   nh = 1;
   int fresh = 1;  // r was recomputed from the design at this vertex
+  int exact = 0;  // r is the exact-sign residual of this vertex (exact_residual)
   for (;;) {
     snap_g<G>(s);
     gsync<G>();
     if (!s.flag) { exit_code = 4; break; }  // singular basis: give up (status MAX_ITERS)
     // r: moved along the edge by the last step (below), recomputed from the
     // design at the first vertex and every kReanchor pivots
-    if (it % kReanchor == 0) { recompute_r<G>(s); fresh = 1; }
+    if (it % kReanchor == 0 && !exact) { recompute_r<G>(s); fresh = 1; }
     for (int w = tid; w < s.maskw; w += G) s.mask[w] = 0u;
     gsync<G>();
     if (tid == 0)
@@ -1899,7 +1998,7 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     gsync<G>();
     // column sums g_c = -sum_{rows not in basis} sign(r_i) x_ic: in full at
     // the first pivot, then from the rows that changed (colsums)
-    colsums<G>(s, it == 0);
+    colsums<G>(s, it == 0 || exact);
     gsync<G>();
     if (warp == 0) mult_solve<G>(s);
     if (G == 32) refine(s, s.mu, s.hv, true);
@@ -1907,6 +2006,14 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     if (warp == 0) mult_pick(s, it < max_piv);
     gsync<G>();
     const int q = s.q;
+    if (q < 0 && !exact) {
+      // the test passed on float32 residuals: repeat it at this vertex
+      // with every residual's sign exact before accepting
+      exact_residual<G>(s);
+      exact = 1;
+      fresh = 1;
+      continue;
+    }
     if (q < 0) { *is_opt = 1; *nonunique = s.iter; exit_code = 0; break; }
     if (cycled) {
       // a basis repeated under Bland's rule: each iteration is a function
@@ -1946,6 +2053,7 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
     // the line search's factor; zero on the basis rows that stay)
     axpy_r<G>(s, s.colp, ts);
     fresh = 0;
+    exact = 0;
     if (warp == 0) {
       for (int c = lane; c < p; c += 32) s.bv[c] += ts * s.dv[c];
       __syncwarp();

@@ -348,6 +348,45 @@ struct TFit {
     return false;
   }
 
+  // r = y - X b at the vertex of the current basis with every sign exact
+  // (a float32 residual within rounding of zero can take the wrong side,
+  // and its sign enters the multipliers): each r_i in float32 with the
+  // magnitude S_i = |y_i| + sum_c |x_ic b_c| of its terms, whose rounding
+  // error stays below 2^-14 S_i for p <= 256; rows inside that band again
+  // in FP64 at b + e (e: one correction solved from the basis equations'
+  // FP64 residual), 0 within FP64 resolution (2^-40 of the magnitude of
+  // its terms).  Needs the current basis factored; dv is scratch.
+  __device__ void exact_residual() {
+    for (int e = 0; e < p; ++e) {
+      const int cd = code[e];
+      double acc = 0.0;
+      if (cd >= 0) {  // coordinate equations hold exactly (snap)
+        for (int c = 0; c < p; ++c) acc += (double)x(cd, c) * (double)bv[c];
+        acc = (double)yv(cd) - acc;
+      }
+      dv[e] = (float)acc;
+    }
+    lu_solve(dv);
+    for (int i = 0; i < n; ++i) {
+      float acc = yv(i), mag = fabsf(acc);
+      for (int c = 0; c < p; ++c) {
+        const float t = x(i, c) * bv[c];
+        acc -= t;
+        mag += fabsf(t);
+      }
+      if (fabsf(acc) <= 0x1p-14f * mag) {
+        double a = (double)yv(i), m = fabs(a);
+        for (int c = 0; c < p; ++c) {
+          const double t = (double)x(i, c) * ((double)bv[c] + (double)dv[c]);
+          a -= t;
+          m += fabs(t);
+        }
+        acc = fabs(a) <= 0x1p-40 * m ? 0.f : (float)a;
+      }
+      r[i] = acc;
+    }
+  }
+
   // b := the vertex of the current basis (phantom coordinates keep their
   // value), r recomputed.  False when the basis matrix is singular.
   __device__ bool snap() {
@@ -415,39 +454,49 @@ struct TFit {
     nonunique = 0;
     for (;;) {
       if (!snap()) break;
-      // mu = -g, row part with compensated sums
-      for (int c = 0; c < p; ++c) { mu[c] = 0.f; tv[c] = 0.f; }
-      for (int i = 0; i < n; ++i) {
-        if (in_basis_row(i)) continue;
-        float sg = fsign(r[i]);
-        if (sg != 0.f)
-          for (int c = 0; c < p; ++c) {
-            const float t = sg * x(i, c) - tv[c];
-            const float nb = mu[c] + t;
-            tv[c] = (nb - mu[c]) - t;
-            mu[c] = nb;
-          }
+      int qq, qb, phantoms, atcap;
+      float vmax;
+      for (int exact = 0;; exact = 1) {
+        // mu = -g, row part with compensated sums
+        for (int c = 0; c < p; ++c) { mu[c] = 0.f; tv[c] = 0.f; }
+        for (int i = 0; i < n; ++i) {
+          if (in_basis_row(i)) continue;
+          float sg = fsign(r[i]);
+          if (sg != 0.f)
+            for (int c = 0; c < p; ++c) {
+              const float t = sg * x(i, c) - tv[c];
+              const float nb = mu[c] + t;
+              tv[c] = (nb - mu[c]) - t;
+              mu[c] = nb;
+            }
+        }
+        for (int c = 0; c < p; ++c) {
+          bool real = false;
+          for (int k = 0; k < p; ++k) real |= (code[k] == coord_code(c) && !phan[k]);
+          if (!real) mu[c] -= lam * fsign(bv[c]);
+          hv[c] = mu[c];  // right-hand side (hv is free after the snap)
+        }
+        lu_solve_t(mu);
+        refine(mu, hv, dv, true);
+        qq = -1; qb = -1; phantoms = 0; atcap = 0;
+        int lowest = INT32_MAX;
+        float worst = tol;
+        vmax = 0.f;
+        for (int k = 0; k < p; ++k) {
+          float cap = code[k] >= 0 ? 1.f : (phan[k] ? 0.f : lam);
+          float viol = fabsf(mu[k]) - cap;
+          if (phan[k]) phantoms++;
+          else if (viol > -1e-4f * fmaxf(1.f, cap)) atcap++;
+          if (viol > worst) { worst = viol; qq = k; }
+          if (viol > tol && code[k] < lowest) { lowest = code[k]; qb = k; }
+          vmax = fmaxf(vmax, viol);
+        }
+        if (bland) qq = qb;  // Bland's rule: lowest id
+        if (qq >= 0 || exact) break;
+        // the test passed on float32 residuals: repeat it at this vertex
+        // with every residual's sign exact before accepting
+        exact_residual();
       }
-      for (int c = 0; c < p; ++c) {
-        bool real = false;
-        for (int k = 0; k < p; ++k) real |= (code[k] == coord_code(c) && !phan[k]);
-        if (!real) mu[c] -= lam * fsign(bv[c]);
-        hv[c] = mu[c];  // right-hand side (hv is free after the snap)
-      }
-      lu_solve_t(mu);
-      refine(mu, hv, dv, true);
-      int qq = -1, qb = -1, lowest = INT32_MAX, phantoms = 0, atcap = 0;
-      float worst = tol, vmax = 0.f;
-      for (int k = 0; k < p; ++k) {
-        float cap = code[k] >= 0 ? 1.f : (phan[k] ? 0.f : lam);
-        float viol = fabsf(mu[k]) - cap;
-        if (phan[k]) phantoms++;
-        else if (viol > -1e-4f * fmaxf(1.f, cap)) atcap++;
-        if (viol > worst) { worst = viol; qq = k; }
-        if (viol > tol && code[k] < lowest) { lowest = code[k]; qb = k; }
-        vmax = fmaxf(vmax, viol);
-      }
-      if (bland) qq = qb;  // Bland's rule: lowest id
       if (qq < 0) { is_opt = 1; nonunique = phantoms > 0 || atcap > 0; break; }
       if (cycled) {
         if (vmax <= kStallTolFactor * tol) { is_opt = 1; nonunique = 1; }
