@@ -1984,21 +1984,24 @@ __device__ __noinline__ int polish(St& s, int max_piv, int* is_opt, int* nonuniq
   int fresh = 1;  // r was recomputed from the design at this vertex
   int exact = 0;  // r is the exact-sign residual of this vertex (exact_residual)
   for (;;) {
-    snap_g<G>(s);
-    gsync<G>();
-    if (!s.flag) { exit_code = 4; break; }  // singular basis: give up (status MAX_ITERS)
-    // r: moved along the edge by the last step (below), recomputed from the
-    // design at the first vertex and every kReanchor pivots
-    if (it % kReanchor == 0 && !exact) { recompute_r<G>(s); fresh = 1; }
-    for (int w = tid; w < s.maskw; w += G) s.mask[w] = 0u;
-    gsync<G>();
-    if (tid == 0)
-      for (int k = 0; k < p; ++k)
-        if (s.code[k] >= 0) s.mask[s.code[k] >> 5] |= 1u << (s.code[k] & 31);
-    gsync<G>();
+    if (!exact) {  // the retest (exact) stays at the vertex: factors, b and mask hold
+      snap_g<G>(s);
+      gsync<G>();
+      if (!s.flag) { exit_code = 4; break; }  // singular basis: give up (status MAX_ITERS)
+      // r: moved along the edge by the last step (below), recomputed from
+      // the design at the first vertex and every kReanchor pivots
+      if (it % kReanchor == 0) { recompute_r<G>(s); fresh = 1; }
+      for (int w = tid; w < s.maskw; w += G) s.mask[w] = 0u;
+      gsync<G>();
+      if (tid == 0)
+        for (int k = 0; k < p; ++k)
+          if (s.code[k] >= 0) s.mask[s.code[k] >> 5] |= 1u << (s.code[k] & 31);
+      gsync<G>();
+    }
     // column sums g_c = -sum_{rows not in basis} sign(r_i) x_ic: in full at
-    // the first pivot, then from the rows that changed (colsums)
-    colsums<G>(s, it == 0 || exact);
+    // the first pivot, then from the rows that changed (colsums; in the
+    // retest, the rows whose exact sign differs from the float32 one)
+    colsums<G>(s, it == 0 && !exact);
     gsync<G>();
     if (warp == 0) mult_solve<G>(s);
     if (G == 32) refine(s, s.mu, s.hv, true);
