@@ -144,6 +144,44 @@ def test_vertex_from_basis_codes_reproduces_the_oracle():
     assert checked >= 2
 
 
+def test_vertex_multiplier_check_agrees_with_the_oracle_certificate():
+    # the large-workload test falls back on the vertex's own multipliers
+    # where the oracle's certificate takes a row within its zero threshold
+    # for one on its hyperplane; away from that case the two must agree:
+    # True at the oracle's optimal bases, False at other vertices
+    from test_gpu_large import _kkt_at_vertex, _vertex
+    rng = np.random.default_rng(11)
+    seen = {True: 0, False: 0}
+    for n, p in [(60, 3), (150, 6)]:
+        X = rng.standard_normal((n, p))
+        y = X @ np.where(rng.random(p) < 0.5, rng.uniform(-2, 2, p), 0.0) + rng.laplace(0, 0.5, n)
+        for frac in (0.5, 0.1, 0.01):
+            lam = frac * oracle.lambda_max(X, y)
+            r = oracle.fit_path(X, y, [lam])
+            cands = [r["basis"][0]] if r["status"][0] == oracle.FIT_OK else []
+            for _ in range(12):
+                k = rng.integers(0, p + 1)
+                rows = rng.choice(n, k, replace=False)
+                cols = rng.choice(p, p - k, replace=False)
+                cands.append(np.concatenate([rows, -(cols + 1)]).astype(np.int32))
+            for codes in cands:
+                try:
+                    bv = _vertex(X, y, codes)
+                except np.linalg.LinAlgError:
+                    continue
+                res = y - X @ bv
+                off = np.ones(n, bool)
+                off[codes[codes >= 0]] = False
+                if np.any(np.abs(res[off]) <= 1e-6 * max(1.0, np.abs(y).max())):
+                    continue  # a row on (or near) its hyperplane: degenerate
+                F = oracle.objective(X, y, bv, lam)
+                gap, _ = oracle.certify(X, y, bv, lam)
+                want = bool(gap <= 1e-7 * max(1.0, F))
+                assert _kkt_at_vertex(X, y, codes, lam) == want, (n, p, frac, codes)
+                seen[want] += 1
+    assert seen[True] >= 4 and seen[False] >= 20, seen
+
+
 def test_exact_family_stays_exact_in_float32():
     # premise of the GPU test that compares chop-only fits bit for bit: on
     # these problems the oracle's results (and so every key, residual and
